@@ -1,0 +1,361 @@
+"""Benchmark: SPH pair interactions per second (density + force) of the
+sorted cell-pair path on one GB300, with the FP32 roofline fraction of the
+dominant sweep kernel and the forward+adjoint / forward time ratio.
+
+One step = the whole path on one batch: decomposition build (Morton sort,
+octree, tasks, 13-direction sorts), density with the smoothing-length
+solve, ghost, force, and the adjoint of L = sum (rho - 1)^2 + sum |a|^2.
+Units per step = directed density interactions (r < h_i, self included) +
+unordered force pairs (r < max(h_i, h_j)), both at the solved h.
+
+Default workload: 128^3 multi-resolution box (jittered lattice with 20 %
+of sites removed + Plummer clump holding 20 % of the particles).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH pair interactions/s (density+force), % of FP32 roofline; fwd+adj/fwd time"
+UNIT = "interactions/s"
+# canonical FP32-pipe instructions per unit (density: per directed
+# interaction; force: per unordered pair counted once)
+INSTR = {0: 18.0, 2: 40.0}
+PHASE_NAMES = {0: "density", 1: "density_d2", 2: "force", 3: "force_adjoint", 4: "density_adjoint"}
+SMS = 152
+LANES = 128
+
+
+def workload(name):
+    import synth.configs as C
+    if name == "multires128":
+        return C.multires(128, seed=2)
+    if name == "multires64":
+        return C.multires(64, seed=2)
+    if name == "lattice16":
+        return C.uniform_lattice(16, seed=1)
+    if name == "sinusoid64":
+        return C.sinusoid(64, seed=4)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample_rate(d, seconds_target=15.0, seed=0, sample=None):
+    """Time the FP64 oracle on a bounded random sample of the workload:
+    units of the sampled particles (their directed density interactions
+    plus half their force partners) per second of oracle time."""
+    from oracle import sph_oracle as O
+    n = d["x"].shape[0]
+    rng = np.random.default_rng(seed)
+    S = sample or 256
+    idx = np.sort(rng.choice(n, S, replace=False))
+    t0 = time.perf_counter()
+    r = O.evaluate_sample(d["x"], d["m"], d["u"], idx, v=d["v"])
+    dt = time.perf_counter() - t0
+    units = float(np.sum(r["count"]) + 0.5 * np.sum(r["force_count"]))
+    return dict(value=units / dt, seconds=dt, sample=int(S), units=units)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    d = workload(args.workload)
+    S = args.ref_sample
+    vals, secs = [], []
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample_rate(d, seed=k, sample=S)
+        if k >= args.warmup:
+            vals.append(r["value"])
+            secs.append(r["seconds"])
+    v = float(np.mean(vals))
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "particles": int(d["x"].shape[0]),
+                   "sample_per_step": S},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{S} random particles of {args.workload} per step, evaluated "
+                                   "from scratch (h solve of the sample and its force partners, "
+                                   "density, force); units = their density interactions + half "
+                                   "their force partners"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="multires128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--kahan", type=int, default=1)
+    ap.add_argument("--block-max", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__ as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    g.build()
+    from paper_1404_2303_gb300 import SPH
+
+    d = workload(args.workload)
+    n = d["x"].shape[0]
+    dev = torch.device("cuda", local)
+    # inputs resident in HBM
+    pos = torch.tensor(d["x"], device=dev, dtype=torch.float64)
+    m = torch.tensor(d["m"], device=dev)
+    u = torch.tensor(d["u"], device=dev)
+    vel = torch.tensor(d["v"], device=dev)
+    params = {"kahan": args.kahan}
+    if args.block_max:
+        params["block_max"] = args.block_max
+    if args.warps:
+        params["warps_per_cta"] = args.warps
+    sph = SPH(**params)
+    stream = torch.cuda.current_stream()
+
+    ev = {}
+
+    def step(pos, m, u, vel, mark=False):
+        if mark:
+            ev.setdefault("f0", []).append(torch.cuda.Event(enable_timing=True))
+            ev["f0"][-1].record(stream)
+        sph.build(pos)
+        den = sph.density(m)
+        acc, dudt, _ = sph.force(u, vel)
+        if mark:
+            ev.setdefault("f1", []).append(torch.cuda.Event(enable_timing=True))
+            ev["f1"][-1].record(stream)
+        g_pos, g_m, g_u = sph.adjoint(2.0 * (den["rho"] - 1.0), 2.0 * acc, None)
+        if mark:
+            ev.setdefault("a1", []).append(torch.cuda.Event(enable_timing=True))
+            ev["a1"][-1].record(stream)
+        return den, acc, dudt, g_pos, g_m, g_u
+
+    for _ in range(args.warmup):
+        out = step(pos, m, u, vel)
+    torch.cuda.synchronize()
+    # units per step (counted at the solved h, outside the timed region)
+    den = out[0]
+    sph.density_fixed_h(m, den["h"], count=True)
+    sph.force(u, vel, count=True)
+    st = sph.stats()
+    units = st["density_interactions"] + st["force_pairs"]
+
+    # ---- timed region: K full steps, device-resident inputs
+    sph.profile(True)
+    launches0 = sph.launch_count()
+    clk = ClockSampler(local)
+    clk.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        out = step(pos, m, u, vel, mark=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    launches = sph.launch_count() - launches0
+    ms = t0.elapsed_time(t1) / args.steps
+    fwd_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(ev["f0"], ev["f1"])]))
+    adj_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(ev["f1"], ev["a1"])]))
+    st = sph.stats()
+    sph.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units * world / (ms / 1e3)
+
+    # ---- end to end through the public API: pinned host inputs, host outputs
+    hpos = torch.tensor(d["x"], dtype=torch.float64).pin_memory()
+    hm = torch.tensor(d["m"]).pin_memory()
+    hu = torch.tensor(d["u"]).pin_memory()
+    hv = torch.tensor(d["v"]).pin_memory()
+    outs_host = None
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dp = hpos.to(dev, non_blocking=True)
+        dm = hm.to(dev, non_blocking=True)
+        du_ = hu.to(dev, non_blocking=True)
+        dv = hv.to(dev, non_blocking=True)
+        den, acc, dudt, g_pos, g_m, g_u = step(dp, dm, du_, dv)
+        outs_host = [t.to("cpu", non_blocking=True) for t in (den["rho"], den["h"], acc, dudt, g_pos, g_m, g_u)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    h2d = sum(t.numel() * t.element_size() for t in (hpos, hm, hu, hv))
+    d2h = sum(t.numel() * t.element_size() for t in outs_host)
+
+    # ---- roofline of the dominant sweep kernel
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_alu = SMS * LANES * sm_max * 1e6  # FP32 lane-instructions/s at the maximum SM clock
+    phase_ms = st["sweep_ms"]
+    dom = int(np.argmax(phase_ms[:5]))
+    kernels = {}
+    for ph in range(5):
+        if st["sweep_launches"][ph] == 0:
+            continue
+        L = st["sweep_launches"][ph]
+        u_ph = st["sweep_units"][ph]
+        if ph >= 2:
+            u_ph = u_ph / 2.0  # ordered -> unordered pairs
+        kernels[PHASE_NAMES[ph]] = {
+            "launches_per_step": L / args.steps, "ms_per_launch": phase_ms[ph] / L,
+            "units_per_launch": u_ph / L,
+            "share_of_step": phase_ms[ph] / args.steps / ms,
+        }
+    roof = None
+    dname = PHASE_NAMES[dom]
+    if dom in INSTR and st["sweep_launches"][dom] > 0:
+        k = kernels[dname]
+        achieved = k["units_per_launch"] * INSTR[dom] / (k["ms_per_launch"] / 1e3)
+        roof = {"kernel": f"k_sweep<{dname}>", "bound": "alu", "achieved": achieved / 1e12,
+                "peak": peak_alu / 1e12, "unit": "T FP32-instr/s",
+                "frac": achieved / peak_alu, "traffic": None,
+                "peak_source": f"{SMS} SMs x {LANES} FP32 lanes x {sm_max:.0f} MHz "
+                               f"(sm_max_mhz of {pk_kind} peaks)",
+                "instr_per_unit": INSTR[dom]}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            r = oracle_sample_rate(d, sample=args.ref_sample)
+            cpu = {"value": r["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"{r['sample']} random particles of {args.workload}, evaluated from "
+                             f"scratch in {r['seconds']:.1f} s (h solve of the sample and its "
+                             "force partners, density, force)"}
+        except Exception as e:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {e}"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "particles": n,
+                       "units_per_step": units, "density_interactions": st["density_interactions"],
+                       "force_pairs": st["force_pairs"],
+                       "step": "build+density(h-solve)+ghost+force+adjoint",
+                       "l2": "working set per step > L2 (sorted lists alone ~%d MB)" % (st["sorted_entries"] * 8 // 2**20),
+                       "kahan": args.kahan, "parallelism": f"replicas x{world}"},
+            "fwd_ms": fwd_ms, "adj_ms": adj_ms, "fwd_adj_over_fwd": (fwd_ms + adj_ms) / fwd_ms,
+            "fwd_value": units / (fwd_ms / 1e3),
+            "clocks": clocks,
+            "e2e": {"value": units * world / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernels": kernels,
+            "decomposition": {k: st[k] for k in ("ncell", "nleaf", "nblock", "nself", "npair", "ndt",
+                                                 "max_depth", "newton_iters", "rebuilds")},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,570 @@
+// C ABI entry points (include/sphgb.h) and the per-particle kernels around
+// the sweeps: gathers into cell order, the smoothing-length update of
+// Eq. (nneigh), the ghost step, and scatters back to the caller's order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr float SIGMA = 2.546479089470325f;  // 8/pi
+
+enum : int { HF_ACTIVE = 1, HF_HI_VALID = 2, HF_LIMIT = 4 };
+
+__global__ void k_fill_mass(long long n, const int* perm, const float* m, float4* pos4) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < n) pos4[s].w = m[perm[s]];
+}
+
+__global__ void k_gather(long long n, const int* perm, const float* in, float* out) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < n) out[s] = in[perm[s]];
+}
+
+__global__ void k_scatter(long long n, const int* perm, const float* in, float* out) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < n) out[perm[s]] = in[s];
+}
+
+__global__ void k_scatter_i(long long n, const int* perm, const int* in, int* out) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < n) out[perm[s]] = in[s];
+}
+
+__global__ void k_check_h(long long n, const float* h, const float* hlim, int* status) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  float v = h[s];
+  if (!(v > 0.f) || v > hlim[s]) atomicOr(status, ST_CELL_LIMIT);
+}
+
+// ---- smoothing-length solve (Eq. (nneigh)): FP64 bracket, Newton steps
+__global__ void k_hsolve_init(long long n, float* h, const float* hlim, double* lo, double* hi,
+                              int* flag) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  float hl = hlim[s];
+  float v = h[s];
+  if (!(v > 0.f) || v > hl) v = hl;
+  h[s] = v;
+  lo[s] = 0.0;
+  hi[s] = (double)hl;
+  flag[s] = HF_ACTIVE;
+}
+
+__global__ void k_hsolve_update(long long n, float* h, const float* hlim, const float* nngb,
+                                const float* dnngb, double* lo, double* hi, int* flag, float n_ngb,
+                                float tol, int* nactive, int* nlimit) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int fl = flag[s];
+  if (!(fl & HF_ACTIVE)) return;
+  double hd = (double)h[s];
+  double f = (double)nngb[s] - (double)n_ngb;
+  if (fabs(f) <= (double)tol * (double)n_ngb) {
+    flag[s] = fl & ~HF_ACTIVE;
+    return;
+  }
+  double L = lo[s], H = hi[s];
+  double hl = (double)hlim[s];
+  if (f < 0) {
+    L = hd;
+    if (hd >= hl) {  // the root lies beyond what this decomposition covers
+      flag[s] = HF_LIMIT;
+      atomicAdd(nlimit, 1);
+      return;
+    }
+  } else {
+    H = hd;
+    fl |= HF_HI_VALID;
+  }
+  double dN = (double)dnngb[s];
+  double hn = dN > 0 ? hd - f / dN : -1.0;
+  if (fl & HF_HI_VALID) {
+    if (!(hn > L && hn < H)) hn = 0.5 * (L + H);
+    if (H - L <= 2.4e-7 * hd) {  // bracket below FP32 resolution
+      lo[s] = L;
+      hi[s] = H;
+      flag[s] = fl & ~HF_ACTIVE;
+      return;
+    }
+  } else {
+    if (!(hn > L)) hn = 2.0 * hd;
+    hn = fmin(hn, hl);
+  }
+  float hf = (float)hn;
+  lo[s] = L;
+  hi[s] = H;
+  if (hf == h[s]) {
+    flag[s] = fl & ~HF_ACTIVE;
+    return;
+  }
+  h[s] = hf;
+  flag[s] = fl;
+  atomicAdd(nactive, 1);
+}
+
+__global__ void k_block_active(int nblock, const int* b_first, const int* b_count, const int* flag,
+                               int* act) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= nblock) return;
+  int f = b_first[warp], c = b_count[warp];
+  int any = 0;
+  for (int k = lane; k < c; k += 32) any |= flag[f + k] & HF_ACTIVE;
+  any = __any_sync(0xffffffffu, any);
+  if (lane == 0) act[warp] = any;
+}
+
+__global__ void k_rebuild_guess(long long n, const float* h, const float* hlim, const int* flag,
+                                float* hg) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  hg[s] = (flag[s] & HF_LIMIT) ? 1.5f * hlim[s] : h[s];
+}
+
+// ---- ghost step (text after Eq. (dudt)) and force-side per-particle data
+__global__ void k_ghost(long long n, const int* perm, const float* h, const float4* pos4,
+                        const float* rho, const float* drho, const float* u, const float* vel,
+                        float gamma, float* omega, float* Avec, float* u_s, float4* vel4,
+                        float4* fdat) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int p = perm[s];
+  float hv = h[s], r = rho[s];
+  float om = 1.f + hv * drho[s] / (3.f * r);
+  float uu = u[p];
+  float P = (gamma - 1.f) * r * uu;
+  float A = P / (om * r * r);
+  float hi = 1.f / hv;
+  float hi2 = hi * hi;
+  float C = 6.f * SIGMA * A * hi2 * hi2;
+  omega[s] = om;
+  Avec[s] = A;
+  u_s[s] = uu;
+  float4 v = make_float4(0.f, 0.f, 0.f, hi);
+  if (vel) {
+    v.x = vel[3 * (long long)p];
+    v.y = vel[3 * (long long)p + 1];
+    v.z = vel[3 * (long long)p + 2];
+  }
+  vel4[s] = v;
+  fdat[s] = make_float4(pos4[s].w * C, __fmul_rn(hv, hv), C, A);
+}
+
+__global__ void k_scatter_acc(long long n, const int* perm, const float4* acc4, float* acc,
+                              float* dudt) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int p = perm[s];
+  float4 a = acc4[s];
+  acc[3 * (long long)p] = a.x;
+  acc[3 * (long long)p + 1] = a.y;
+  acc[3 * (long long)p + 2] = a.z;
+  if (dudt) dudt[p] = a.w;
+}
+
+__global__ void k_sum_i32(long long n, const int* v, unsigned long long* out) {
+  __shared__ unsigned long long sm[TPB / 32];
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  unsigned long long x = s < n ? (unsigned long long)v[s] : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < TPB / 32; ++k) t += sm[k];
+    atomicAdd(out, t);
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static int status_from_word(int w) {
+  if (w & ST_CAPACITY) return SPH_ERR_CAPACITY;
+  if (w & ST_TIMEOUT) return SPH_ERR_TIMEOUT;
+  if (w & ST_CELL_LIMIT) return SPH_ERR_CELL_LIMIT;
+  if (w & ST_NOT_CONVERGED) return SPH_ERR_H_NOT_CONVERGED;
+  if (w & ST_BAD_INDEX) return SPH_ERR_CUDA;
+  return SPH_OK;
+}
+
+static int read_status(sph_ctx* c, cudaStream_t s) {
+  int w = 0;
+  SPH_CUDA(cudaMemcpyAsync(&w, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
+  if (w) SPH_CUDA(cudaMemsetAsync(c->status.p, 0, sizeof(int), s));
+  return status_from_word(w);
+}
+
+static int ensure_state(sph_ctx* c) {
+  const size_t n = (size_t)c->n;
+  DBuf* f1[] = {&c->rho, &c->drho, &c->nngb, &c->dnngb, &c->d2rho, &c->omega, &c->Avec, &c->u_s};
+  for (DBuf* b : f1) SPH_TRY(dbuf_ensure(*b, 4 * n));
+  SPH_TRY(dbuf_ensure(c->fdat, 16 * n));
+  SPH_TRY(dbuf_ensure(c->vel4, 16 * n));
+  SPH_TRY(dbuf_ensure(c->acc4, 16 * n));
+  SPH_TRY(dbuf_ensure(c->cnt_i, 4 * n));
+  SPH_TRY(dbuf_ensure(c->h_lo, 8 * n));
+  SPH_TRY(dbuf_ensure(c->h_hi, 8 * n));
+  SPH_TRY(dbuf_ensure(c->h_flag, 4 * n));
+  SPH_TRY(dbuf_ensure(c->blk_active, 4 * (size_t)(c->nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->tmp_a, 64));
+  return SPH_OK;
+}
+
+static int count_total(sph_ctx* c, unsigned long long* out, cudaStream_t s) {
+  unsigned long long* d = c->counters.as<unsigned long long>() + 1;
+  SPH_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), s));
+  { k_sum_i32<<<div_up(c->n, TPB), TPB, 0, s>>>(c->n, c->cnt_i.as<int>(), d); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_CUDA(cudaMemcpyAsync(out, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
+  return SPH_OK;
+}
+
+extern "C" {
+
+void sph_default_params(sph_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n_ngb = 48.0f;
+  p->gamma = 5.0f / 3.0f;
+  p->split_count = 300;
+  p->split_frac = 0.875f;
+  p->block_max = 128;
+  p->max_newton = 64;
+  p->max_rebuild = 4;
+  p->kahan = 1;
+  p->morton_bits = 16;
+  p->h_tol = 1.0f / 524288.0f;  // 2^-19
+  p->warps_per_cta = 4;
+  p->ctas_per_sm = 0;
+}
+
+int sph_create(const sph_params* p, sph_ctx** out) {
+  if (!out) return SPH_ERR_INVALID_ARG;
+  *out = nullptr;
+  sph_params q;
+  if (p) q = *p; else sph_default_params(&q);
+  if (!(q.n_ngb > 32.f / 3.f) || !(q.gamma > 1.f) || q.split_count < 1 || !(q.split_frac > 0.f) ||
+      q.block_max < 32 || q.block_max > 256 || q.max_newton < 1 || q.max_rebuild < 0 ||
+      q.morton_bits < 8 || q.morton_bits > 20 || !(q.h_tol > 0.f) || q.warps_per_cta < 1 ||
+      q.warps_per_cta > 8 || q.ctas_per_sm < 0)
+    return SPH_ERR_INVALID_ARG;
+  sph_ctx* c = new sph_ctx();
+  c->prm = q;
+  c->kbits = q.morton_bits;
+  int r;
+  if ((r = dbuf_ensure(c->status, 64)) != SPH_OK || (r = dbuf_ensure(c->counters, 64)) != SPH_OK ||
+      (r = dbuf_ensure(c->queue, 64)) != SPH_OK) {
+    sph_destroy(c);
+    return r;
+  }
+  cudaMemset(c->status.p, 0, 64);
+  cudaMemset(c->counters.p, 0, 64);
+  *out = c;
+  return SPH_OK;
+}
+
+void sph_destroy(sph_ctx* c) {
+  if (!c) return;
+  DBuf* all[] = {&c->d_box_off, &c->d_box_L, &c->d_box_t, &c->d_top_base, &c->keys, &c->keys_alt,
+                 &c->perm, &c->perm_alt, &c->xs, &c->pos4, &c->h, &c->hguess, &c->hlim, &c->pnode,
+                 &c->n_first, &c->n_count, &c->n_parent, &c->n_child0, &c->n_top, &c->n_flags,
+                 &c->n_need, &c->n_ijk, &c->n_box, &c->n_hmax, &c->n_hbuild, &c->n_hlim,
+                 &c->n_sbase, &c->t_cur, &c->t_next, &c->t_final_pair, &c->t_final_self, &c->t_cnt,
+                 &c->t_cnt2, &c->t_off, &c->t_off2, &c->b_first, &c->b_count, &c->b_leaf,
+                 &c->b_dtoff, &c->b_order, &c->b_cost, &c->dt_cj, &c->dt_code, &c->dt_shift,
+                 &c->adj_off, &c->adj_list, &c->s_key, &c->s_idx, &c->rho, &c->drho, &c->nngb,
+                 &c->dnngb, &c->d2rho, &c->omega, &c->Avec, &c->fdat, &c->vel4, &c->u_s, &c->acc4,
+                 &c->cnt_i, &c->h_lo, &c->h_hi, &c->h_flag, &c->blk_active, &c->adj4, &c->adj4b, &c->g_A,
+                 &c->g_rho_s, &c->g_drho_s, &c->g_h_s, &c->g_u_s, &c->g_x4,
+                 &c->prof_units, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
+                 &c->tmp_b, &c->tmp_c};
+  for (DBuf* b : all) dbuf_free(*b);
+  for (auto& e : c->ev_pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+int sph_build_batch(sph_ctx* c, int32_t nbox, const int64_t* offsets, const double* boxes,
+                    const double* pos, const float* h_guess, void* stream) {
+  if (!c || nbox < 1 || nbox > SPH_MAX_BOX || !offsets || !boxes || !pos)
+    return SPH_ERR_INVALID_ARG;
+  if (offsets[0] != 0) return SPH_ERR_INVALID_ARG;
+  for (int b = 0; b < nbox; ++b)
+    if (offsets[b + 1] <= offsets[b] || !(boxes[b] > 0)) return SPH_ERR_INVALID_ARG;
+  long long n = offsets[nbox];
+  if (n <= 0 || n >= (1ll << 31) / 16) return SPH_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  c->built = c->have_density = c->have_force = false;
+  c->have_d2 = 0;
+  c->n = n;
+  c->nbox = nbox;
+  c->box_off.assign(offsets, offsets + nbox + 1);
+  c->box_L.assign(boxes, boxes + nbox);
+  c->box_t.assign(nbox, 2);
+  SPH_TRY(dbuf_ensure(c->d_box_off, sizeof(long long) * (nbox + 1)));
+  SPH_TRY(dbuf_ensure(c->d_box_L, sizeof(double) * nbox));
+  SPH_TRY(dbuf_ensure(c->d_box_t, sizeof(int) * nbox));
+  SPH_TRY(dbuf_ensure(c->d_top_base, sizeof(int) * (nbox + 1)));
+  SPH_CUDA(cudaMemcpyAsync(c->d_box_off.p, c->box_off.data(), sizeof(long long) * (nbox + 1),
+                           cudaMemcpyHostToDevice, s));
+  SPH_CUDA(cudaMemcpyAsync(c->d_box_L.p, c->box_L.data(), sizeof(double) * nbox,
+                           cudaMemcpyHostToDevice, s));
+  SPH_CUDA(cudaMemsetAsync(c->status.p, 0, sizeof(int), s));
+  SPH_TRY(build_decomposition(c, pos, h_guess, s));
+  SPH_TRY(ensure_state(c));
+  int st = read_status(c, s);
+  if (st != SPH_OK) return st;
+  c->built = true;
+  return SPH_OK;
+}
+
+int sph_build(sph_ctx* c, int64_t n, const double* pos, double box, const float* h_guess,
+              void* stream) {
+  int64_t off[2] = {0, n};
+  return sph_build_batch(c, 1, off, &box, pos, h_guess, stream);
+}
+
+static int prep_mass(sph_ctx* c, const float* m, cudaStream_t s) {
+  { k_fill_mass<<<div_up(c->n, TPB), TPB, 0, s>>>(c->n, c->perm.as<int>(), m, c->pos4.as<float4>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+int sph_density_fixed_h(sph_ctx* c, const float* m, const float* h, float* rho, float* drho_dh,
+                        float* nngb, float* dnngb_dh, int32_t* count, void* stream) {
+  if (!c || !m || !h || !rho) return SPH_ERR_INVALID_ARG;
+  if (!c->built) return SPH_ERR_NOT_BUILT;
+  cudaStream_t s = as_stream(stream);
+  const long long n = c->n;
+  SPH_TRY(prep_mass(c, m, s));
+  { k_gather<<<div_up(n, TPB), TPB, 0, s>>>(n, c->perm.as<int>(), h, c->h.as<float>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  { k_check_h<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), c->hlim.as<float>(),
+                                           c->status.as<int>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(compute_node_hmax(c, s));
+  SPH_TRY(run_sweep(c, PH_DENSITY, 0, count != nullptr, s));
+  const int* perm = c->perm.as<int>();
+  { k_scatter<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->rho.as<float>(), rho); note_launch(); }
+  { if (drho_dh) k_scatter<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->drho.as<float>(), drho_dh); note_launch(); }
+  { if (nngb) k_scatter<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->nngb.as<float>(), nngb); note_launch(); }
+  { if (dnngb_dh) k_scatter<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->dnngb.as<float>(), dnngb_dh); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  c->have_density = true;
+  c->have_force = false;
+  c->have_d2 = 0;
+  if (count) {
+    { k_scatter_i<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->cnt_i.as<int>(), count); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    unsigned long long tot = 0;
+    SPH_TRY(count_total(c, &tot, s));
+    c->stats.density_interactions = (int64_t)tot;
+    return read_status(c, s);
+  }
+  return SPH_OK;
+}
+
+int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* omega,
+                int32_t* iters, void* stream) {
+  if (!c || !m) return SPH_ERR_INVALID_ARG;
+  if (!c->built) return SPH_ERR_NOT_BUILT;
+  cudaStream_t s = as_stream(stream);
+  const long long n = c->n;
+  SPH_TRY(prep_mass(c, m, s));
+  int total_iters = 0, rebuilds = 0;
+  int* nact = c->tmp_a.as<int>();
+  int* nlim = nact + 1;
+  for (;;) {
+    { k_hsolve_init<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), c->hlim.as<float>(),
+                                                 c->h_lo.as<double>(), c->h_hi.as<double>(),
+                                                 c->h_flag.as<int>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    int host[2] = {1, 0};
+    int it = 0;
+    SPH_CUDA(cudaMemsetAsync(c->blk_active.p, 0, 4 * (size_t)c->nblock, s));
+    for (; it < c->prm.max_newton; ++it) {
+      { k_block_active<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, s>>>(
+          c->nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->h_flag.as<int>(),
+          c->blk_active.as<int>()); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+      SPH_TRY(run_sweep(c, PH_DENSITY, 1, 0, s));
+      SPH_CUDA(cudaMemsetAsync(nact, 0, 2 * sizeof(int), s));
+      { k_hsolve_update<<<div_up(n, TPB), TPB, 0, s>>>(
+          n, c->h.as<float>(), c->hlim.as<float>(), c->nngb.as<float>(), c->dnngb.as<float>(),
+          c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_flag.as<int>(), c->prm.n_ngb,
+          c->prm.h_tol, nact, nlim); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+      SPH_CUDA(cudaMemcpyAsync(host, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      SPH_CUDA(cudaStreamSynchronize(s));
+      if (host[0] == 0) {
+        ++it;
+        break;
+      }
+    }
+    total_iters += it;
+    if (host[0] != 0) {
+      c->stats.newton_iters = total_iters;
+      return SPH_ERR_H_NOT_CONVERGED;
+    }
+    if (host[1] == 0) break;
+    if (rebuilds >= c->prm.max_rebuild) {
+      c->stats.newton_iters = total_iters;
+      return SPH_ERR_CELL_LIMIT;
+    }
+    ++rebuilds;
+    { k_rebuild_guess<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), c->hlim.as<float>(),
+                                                   c->h_flag.as<int>(), c->hguess.as<float>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    SPH_TRY(build_from_guess(c, s));
+    SPH_TRY(ensure_state(c));
+    SPH_TRY(prep_mass(c, m, s));
+  }
+  c->stats.newton_iters = total_iters;
+  c->stats.rebuilds = rebuilds;
+  if (iters) *iters = total_iters;
+  SPH_TRY(compute_node_hmax(c, s));
+  const int* perm = c->perm.as<int>();
+  // Omega for the caller; the full ghost step runs in sph_force
+  { if (h_out) k_scatter<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->h.as<float>(), h_out); note_launch(); }
+  { if (rho) k_scatter<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->rho.as<float>(), rho); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  if (omega) {
+    { k_ghost<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->h.as<float>(), c->pos4.as<float4>(),
+                                           c->rho.as<float>(), c->drho.as<float>(), m, nullptr,
+                                           c->prm.gamma, c->omega.as<float>(), c->Avec.as<float>(),
+                                           c->u_s.as<float>(), c->vel4.as<float4>(),
+                                           c->fdat.as<float4>()); note_launch(); }
+    { k_scatter<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->omega.as<float>(), omega); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  c->have_density = true;
+  c->have_force = false;
+  c->have_d2 = 0;
+  return read_status(c, s);
+}
+
+int sph_force(sph_ctx* c, const float* u, const float* vel, float* acc, float* dudt,
+              int32_t* count, void* stream) {
+  if (!c || !u || !acc) return SPH_ERR_INVALID_ARG;
+  if (!c->have_density) return SPH_ERR_NOT_BUILT;
+  cudaStream_t s = as_stream(stream);
+  const long long n = c->n;
+  const int* perm = c->perm.as<int>();
+  { k_ghost<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->h.as<float>(), c->pos4.as<float4>(),
+                                         c->rho.as<float>(), c->drho.as<float>(), u, vel,
+                                         c->prm.gamma, c->omega.as<float>(), c->Avec.as<float>(),
+                                         c->u_s.as<float>(), c->vel4.as<float4>(),
+                                         c->fdat.as<float4>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(run_sweep(c, PH_FORCE, 0, count != nullptr, s));
+  { k_scatter_acc<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->acc4.as<float4>(), acc, dudt); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  c->have_force = true;
+  if (count) {
+    { k_scatter_i<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->cnt_i.as<int>(), count); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    unsigned long long tot = 0;
+    SPH_TRY(count_total(c, &tot, s));
+    c->stats.force_pairs = (int64_t)(tot / 2);
+    return read_status(c, s);
+  }
+  return SPH_OK;
+}
+
+int sph_pairs_dump(sph_ctx* c, int32_t phase, int64_t cap, int32_t* pi, int32_t* pj,
+                   int64_t* n_out, void* stream) {
+  if (!c || !pi || !pj || !n_out || cap < 0 || (phase != 0 && phase != 1))
+    return SPH_ERR_INVALID_ARG;
+  if (!c->have_density) return SPH_ERR_NOT_BUILT;
+  cudaStream_t s = as_stream(stream);
+  c->dump_pi = pi;
+  c->dump_pj = pj;
+  c->dump_cap = cap;
+  SPH_CUDA(cudaMemsetAsync(c->counters.p, 0, sizeof(unsigned long long), s));
+  if (phase == 1) SPH_TRY(compute_node_hmax(c, s));
+  SPH_TRY(run_sweep(c, phase == 0 ? PH_DUMP_DENSITY : PH_DUMP_FORCE, 0, 0, s));
+  unsigned long long nn = 0;
+  SPH_CUDA(cudaMemcpyAsync(&nn, c->counters.p, sizeof(nn), cudaMemcpyDeviceToHost, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
+  c->dump_pi = c->dump_pj = nullptr;
+  *n_out = (int64_t)nn;
+  if ((long long)nn > cap) return SPH_ERR_CAPACITY;
+  return read_status(c, s);
+}
+
+int sph_profile(sph_ctx* c, int32_t enable) {
+  if (!c) return SPH_ERR_INVALID_ARG;
+  SPH_TRY(prof_resolve(c));
+  for (int k = 0; k < 8; ++k) {
+    c->prof_ms[k] = 0;
+    c->prof_n[k] = 0;
+    c->prof_units_acc[k] = 0;
+  }
+  if (enable) SPH_TRY(dbuf_ensure(c->prof_units, 4096 * sizeof(unsigned long long)));
+  c->profile = enable != 0;
+  return SPH_OK;
+}
+
+int sph_get_stats(sph_ctx* c, sph_stats* out) {
+  if (!c || !out) return SPH_ERR_INVALID_ARG;
+  SPH_TRY(prof_resolve(c));
+  sph_stats st = c->stats;
+  for (int k = 0; k < 8; ++k) {
+    st.sweep_ms[k] = c->prof_ms[k];
+    st.sweep_launches[k] = c->prof_n[k];
+    st.sweep_units[k] = (int64_t)c->prof_units_acc[k];
+  }
+  st.sweep_grid = c->sweep_grid;
+  st.sweep_threads = c->sweep_threads;
+  st.n = c->n;
+  st.nbox = c->nbox;
+  st.ncell = c->ncell;
+  st.nleaf = c->nleaf;
+  st.nblock = c->nblock;
+  st.nself = c->nself;
+  st.npair = c->npair;
+  st.ndt = c->ndt;
+  st.max_depth = c->max_depth;
+  for (int b = 0; b < 8; ++b) st.top_level[b] = b < c->nbox ? c->box_t[b] : 0;
+  st.sorted_entries = c->sorted_entries;
+  *out = st;
+  return SPH_OK;
+}
+
+int sph_sync_status(sph_ctx* c, void* stream) {
+  if (!c) return SPH_ERR_INVALID_ARG;
+  return read_status(c, as_stream(stream));
+}
+
+int64_t sph_launch_count(void) { return (int64_t)launch_count(); }
+
+const char* sph_status_string(int st) {
+  switch (st) {
+    case SPH_OK: return "ok";
+    case SPH_ERR_INVALID_ARG: return "invalid argument";
+    case SPH_ERR_CUDA: return "CUDA runtime error";
+    case SPH_ERR_OOM: return "device out of memory";
+    case SPH_ERR_H_NOT_CONVERGED: return "smoothing-length iteration did not converge";
+    case SPH_ERR_CELL_LIMIT: return "smoothing length exceeds the cell decomposition";
+    case SPH_ERR_NOT_BUILT: return "decomposition or density state missing";
+    case SPH_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SPH_ERR_CAPACITY: return "output capacity exceeded";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

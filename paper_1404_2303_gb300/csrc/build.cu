@@ -1,0 +1,1125 @@
+// Decomposition build: Morton order, the hierarchical cells of Section 3.2,
+// the self/pair task refinement of Fig. SplitCell / SplitPair, per-warp
+// particle blocks, the 13-direction sorted lists of Section 3.3 (blocks
+// sorted in shared memory, parents merged from their sub-cells as in
+// Fig. HierarchySorting) and the per-block interaction lists the sweeps
+// consume.
+#include <algorithm>
+#include <cmath>
+
+#include "geom.cuh"
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int EST_SPLIT = 64;  // count-only split threshold of the h-estimate octree
+
+__device__ __forceinline__ int box_of(const long long* off, int nbox, long long p) {
+  int lo = 0, hi = nbox;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int box_of_node(const int* top_base, int nbox, int id) {
+  int lo = 0, hi = nbox;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (top_base[mid] <= id) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double wrap_pos(double x, double L) {
+  double w = x - L * floor(x / L);
+  if (w >= L) w -= L;
+  if (w < 0) w = 0;
+  return w;
+}
+
+__device__ __forceinline__ int lower_bound_u64(const unsigned long long* a, int lo, int hi,
+                                               unsigned long long v) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- keys
+__global__ void k_keys(const double* pos, long long n, const long long* off, const double* Ls,
+                       int nbox, int K, unsigned long long* keys, int* perm) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int b = box_of(off, nbox, p);
+  double L = Ls[b];
+  double scale = (double)(1u << K) / L;
+  unsigned q[3];
+  for (int k = 0; k < 3; ++k) {
+    double x = wrap_pos(pos[3 * p + k], L);
+    long long v = (long long)floor(x * scale);
+    v = v < 0 ? 0 : (v > (1ll << K) - 1 ? (1ll << K) - 1 : v);
+    q[k] = (unsigned)v;
+  }
+  keys[p] = ((unsigned long long)b << (3 * K)) | morton3(q[0], q[1], q[2]);
+  perm[p] = (int)p;
+}
+
+__global__ void k_gather_pos(const double* pos, const int* perm, long long n, const long long* off,
+                             const double* Ls, int nbox, const float* hg_in, double* xs,
+                             float* hg_out) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int p = perm[s];
+  int b = box_of(off, nbox, p);
+  double L = Ls[b];
+  for (int k = 0; k < 3; ++k) xs[3 * s + k] = wrap_pos(pos[3 * (long long)p + k], L);
+  if (hg_in) hg_out[s] = hg_in[p];
+}
+
+// ---------------------------------------------------------------- octree
+struct NodeArrays {
+  int *first, *count, *parent, *child0, *top, *box;
+  int4* ijk;
+  float* hbuild;
+};
+
+__global__ void k_init_top(int ntop, const int* top_base, const int* box_t, int nbox,
+                           const unsigned long long* keys, int n, int K, NodeArrays na) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ntop) return;
+  int b = box_of_node(top_base, nbox, id);
+  int t = box_t[b];
+  int nb = 1 << t;
+  int loc = id - top_base[b];
+  int ix = loc / (nb * nb), iy = (loc / nb) % nb, iz = loc % nb;
+  unsigned long long m = morton3(ix, iy, iz);
+  int sh = 3 * (K - t);
+  unsigned long long lo = ((unsigned long long)b << (3 * K)) | (m << sh);
+  unsigned long long hi = lo + (1ull << sh);
+  int f = lower_bound_u64(keys, 0, n, lo);
+  int e = lower_bound_u64(keys, f, n, hi);
+  na.first[id] = f;
+  na.count[id] = e - f;
+  na.parent[id] = -1;
+  na.child0[id] = -1;
+  na.top[id] = id;
+  na.box[id] = b;
+  na.ijk[id] = make_int4(ix, iy, iz, t);
+}
+
+// warp per node: max build h and the split decision of Section 3.2 / 4.2
+__global__ void k_node_stats(int g0, int g1, int mode, int split_count, float split_frac, int K,
+                             const float* hs, const double* Ls, NodeArrays na, int* split) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  int node = g0 + warp;
+  if (node >= g1) return;
+  int f = na.first[node], c = na.count[node];
+  int4 ijk = na.ijk[node];
+  double e = Ls[na.box[node]] / (double)(1ll << ijk.w);
+  float half = (float)(0.5 * e);
+  float hm = 0.f;
+  int small = 0;
+  for (int k = lane; k < c; k += 32) {
+    float hv = hs[f + k];
+    hm = fmaxf(hm, hv);
+    small += hv < half ? 1 : 0;
+  }
+  hm = warp_max(hm);
+  small = warp_sum(small);
+  if (lane == 0) {
+    na.hbuild[node] = hm;
+    int s;
+    if (mode == 0)
+      s = (c > split_count) && ((float)small > split_frac * (float)c) && (ijk.w < K);
+    else
+      s = (c > EST_SPLIT) && (ijk.w < K);
+    split[node - g0] = s;
+  }
+}
+
+__global__ void k_make_children(int g0, int g1, int next, const int* split, const int* soff,
+                                const unsigned long long* keys, int K, NodeArrays na) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int node = g0 + i;
+  if (node >= g1 || !split[i]) return;
+  int c0 = next + 8 * soff[i];
+  na.child0[node] = c0;
+  int f = na.first[node], e = f + na.count[node];
+  int4 p = na.ijk[node];
+  int b = na.box[node];
+  int lvl = p.w + 1;
+  int sh = 3 * (K - lvl);
+  for (int k = 0; k < 8; ++k) {
+    int cx = 2 * p.x + ((k >> 2) & 1), cy = 2 * p.y + ((k >> 1) & 1), cz = 2 * p.z + (k & 1);
+    unsigned long long lo = ((unsigned long long)b << (3 * K)) | (morton3(cx, cy, cz) << sh);
+    unsigned long long hi = lo + (1ull << sh);
+    int cf = lower_bound_u64(keys, f, e, lo);
+    int ce = lower_bound_u64(keys, cf, e, hi);
+    int id = c0 + k;
+    na.first[id] = cf;
+    na.count[id] = ce - cf;
+    na.parent[id] = node;
+    na.child0[id] = -1;
+    na.top[id] = na.top[node];
+    na.box[id] = b;
+    na.ijk[id] = make_int4(cx, cy, cz, lvl);
+  }
+}
+
+__global__ void k_leaf_particles(int ncell, const int* first, const int* count, const int* child0,
+                                 int* pnode) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= ncell || child0[warp] >= 0) return;
+  int f = first[warp], c = count[warp];
+  for (int k = lane; k < c; k += 32) pnode[f + k] = warp;
+}
+
+// h estimate from the count-only octree: local number density of the
+// leaf's parent (or of the leaf itself at the top level), turned into the
+// h whose sphere holds N_ngb particles at that density
+__global__ void k_h_estimate(long long n, const int* pnode, const int* parent, const int* count,
+                             const int4* ijk, const int* box, const double* Ls, float n_ngb,
+                             float* hout) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int node = pnode[s];
+  int par = parent[node];
+  int use = par >= 0 ? par : node;
+  double L = Ls[box[use]];
+  double e = L / (double)(1ll << ijk[use].w);
+  double dens = (double)count[use] / (e * e * e);
+  double h = cbrt(3.0 * (double)n_ngb / (4.0 * M_PI * dens));
+  h = fmin(h, 0.24 * L);
+  hout[s] = (float)h;
+}
+
+__global__ void k_relpos(long long n, const unsigned long long* keys, const double* xs,
+                         const double* Ls, const int* box_t, int K, float4* pos4) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  unsigned long long key = keys[s];
+  int b = (int)(key >> (3 * K));
+  int t = box_t[b];
+  unsigned long long tm = (key >> (3 * (K - t))) & ((1ull << (3 * t)) - 1);
+  int ix = compact3(tm >> 2), iy = compact3(tm >> 1), iz = compact3(tm);
+  double e = Ls[b] / (double)(1 << t);
+  float4 v;
+  v.x = (float)(xs[3 * s + 0] - ix * e);
+  v.y = (float)(xs[3 * s + 1] - iy * e);
+  v.z = (float)(xs[3 * s + 2] - iz * e);
+  v.w = 0.f;
+  pos4[s] = v;
+}
+
+// ---------------------------------------------------------------- tasks
+// task: int4 {ci, cj, packed offset/periodic image, type (0 self, 1 pair)}
+__device__ __forceinline__ int top_id(const int* top_base, int b, int n, int x, int y, int z) {
+  return top_base[b] + (x * n + y) * n + z;
+}
+
+__global__ void k_top_tasks(int ntop, const int* top_base, const int* box_t, int nbox,
+                            const int* count, const int* off, int* cnt, int4* out) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ntop) return;
+  int emitted = 0;
+  int base = off ? off[id] : 0;
+  if (count[id] > 0) {
+    int b = box_of_node(top_base, nbox, id);
+    int n = 1 << box_t[b];
+    int loc = id - top_base[b];
+    int ix = loc / (n * n), iy = (loc / n) % n, iz = loc % n;
+    if (out) out[base] = make_int4(id, id, 0, 0);
+    emitted = 1;
+    for (int d = 0; d < SPH_NDIR; ++d) {
+      int ox, oy, oz;
+      dir_offset(d, ox, oy, oz);
+      int x = ix + ox, y = iy + oy, z = iz + oz;
+      int px = x < 0 ? -1 : (x >= n ? 1 : 0);
+      int py = y < 0 ? -1 : (y >= n ? 1 : 0);
+      int pz = z < 0 ? -1 : (z >= n ? 1 : 0);
+      x -= px * n; y -= py * n; z -= pz * n;
+      int nb = top_id(top_base, b, n, x, y, z);
+      if (count[nb] == 0) continue;
+      if (out) out[base + emitted] = make_int4(id, nb, pack_pair(ox, oy, oz, px, py, pz), 1);
+      ++emitted;
+    }
+  }
+  if (cnt) cnt[id] = emitted;
+}
+
+__device__ __forceinline__ bool pair_splits(int a, int b, const int* child0, const float* hb,
+                                            const int4* ijk, const int* box, const double* Ls) {
+  if (child0[a] < 0 || child0[b] < 0) return false;
+  double e = Ls[box[a]] / (double)(1ll << ijk[a].w);
+  float half = (float)(0.5 * e);
+  return hb[a] <= half && hb[b] <= half;
+}
+
+// count (out == nullptr) or emit the children of each task; final tasks go
+// to the self / pair lists
+__global__ void k_refine(int nt, const int4* tasks, const int* child0, const int* count,
+                         const float* hb, const int4* ijk, const int* box, const double* Ls,
+                         int* nchild, int* nfs, int* nfp, const int* off_c, const int* off_s,
+                         const int* off_p, int4* out, int* fin_self, int4* fin_pair, int fs_base,
+                         int fp_base, int* psplit) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  int4 tk = tasks[t];
+  int nc = 0, fs = 0, fp = 0;
+  int oc = off_c ? off_c[t] : 0;
+  if (tk.w == 0) {
+    int c = tk.x;
+    int c0 = child0[c];
+    if (c0 < 0) {
+      fs = 1;
+      if (fin_self) fin_self[fs_base + off_s[t]] = c;
+    } else {
+      for (int a = 0; a < 8; ++a) {
+        int ca = c0 + a;
+        if (count[ca] == 0) continue;
+        if (out) out[oc + nc] = make_int4(ca, ca, 0, 0);
+        ++nc;
+        for (int b2 = a + 1; b2 < 8; ++b2) {
+          int cb = c0 + b2;
+          if (count[cb] == 0) continue;
+          int4 ia = ijk[ca], ib = ijk[cb];
+          if (out)
+            out[oc + nc] = make_int4(ca, cb, pack_pair(ib.x - ia.x, ib.y - ia.y, ib.z - ia.z, 0, 0, 0), 1);
+          ++nc;
+        }
+      }
+    }
+  } else {
+    int a = tk.x, b = tk.y;
+    if (!pair_splits(a, b, child0, hb, ijk, box, Ls)) {
+      fp = 1;
+      if (fin_pair) fin_pair[fp_base + off_p[t]] = tk;
+    } else {
+      if (psplit) {
+        psplit[a] = 1;
+        psplit[b] = 1;
+      }
+      int ox, oy, oz, px, py, pz;
+      unpack_pair(tk.z, ox, oy, oz, px, py, pz);
+      int a0 = child0[a], b0 = child0[b];
+      int n2 = 1 << (ijk[a].w + 1);
+      for (int i = 0; i < 8; ++i) {
+        int ca = a0 + i;
+        if (count[ca] == 0) continue;
+        int4 ia = ijk[ca];
+        for (int j = 0; j < 8; ++j) {
+          int cb = b0 + j;
+          if (count[cb] == 0) continue;
+          int4 ib = ijk[cb];
+          int dx = ib.x + px * n2 - ia.x, dy = ib.y + py * n2 - ia.y, dz = ib.z + pz * n2 - ia.z;
+          if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
+          if (out) out[oc + nc] = make_int4(ca, cb, pack_pair(dx, dy, dz, px, py, pz), 1);
+          ++nc;
+        }
+      }
+    }
+  }
+  if (nchild) {
+    nchild[t] = nc;
+    nfs[t] = fs;
+    nfp[t] = fp;
+  }
+}
+
+__global__ void k_hlim(int g0, int g1, const int* parent, const int* psplit, const int4* ijk,
+                       const int* box, const double* Ls, float* hlim) {
+  int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g1) return;
+  int p = parent[node];
+  double L = Ls[box[node]];
+  if (p < 0) {
+    hlim[node] = (float)(L / (double)(1ll << ijk[node].w));
+  } else {
+    float v = hlim[p];
+    if (psplit[p]) v = fminf(v, (float)(0.5 * L / (double)(1ll << ijk[p].w)));
+    hlim[node] = v;
+  }
+}
+
+__global__ void k_particle_hlim(long long n, const int* pnode, const float* nh, float* ph) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < n) ph[s] = nh[pnode[s]];
+}
+
+// ---------------------------------------------------------------- blocks
+__global__ void k_leaf_nblk(int ncell, const int* child0, const int* count, int bmax, int* nblk) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ncell) return;
+  int c = count[id];
+  nblk[id] = (child0[id] < 0 && c > 0) ? (c + bmax - 1) / bmax : 0;
+}
+
+__global__ void k_make_blocks(int ncell, const int* first, const int* count, const int* nblk,
+                              const int* boff, int* b_first, int* b_count, int* b_leaf,
+                              int* n_blk0) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ncell) return;
+  int nb = nblk[id];
+  n_blk0[id] = nb > 0 ? boff[id] : -1;
+  if (nb == 0) return;
+  int c = count[id], f = first[id];
+  int q = c / nb, r = c % nb;
+  for (int k = 0; k < nb; ++k) {
+    int bi = boff[id] + k;
+    b_first[bi] = f + k * q + min(k, r);
+    b_count[bi] = q + (k < r ? 1 : 0);
+    b_leaf[bi] = id;
+  }
+}
+
+// ---------------------------------------------------------------- sorts
+// one CTA per block: bitonic sort of (key, global index) for each of the
+// 13 directions; ties cannot occur because indices are distinct
+constexpr int SORT_MAX = 256;
+
+__device__ __forceinline__ bool kv_less(float ka, int ia, float kb, int ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+__global__ void __launch_bounds__(SORT_MAX) k_sort_blocks(const int* b_first, const int* b_count,
+                                                          const float4* pos4, float* s_key,
+                                                          int* s_idx) {
+  __shared__ float sk[SORT_MAX];
+  __shared__ int si[SORT_MAX];
+  __shared__ float px[SORT_MAX], py[SORT_MAX], pz[SORT_MAX];
+  int b = blockIdx.x;
+  int f = b_first[b], c = b_count[b];
+  int t = threadIdx.x;
+  if (t < c) {
+    float4 p = pos4[f + t];
+    px[t] = p.x; py[t] = p.y; pz[t] = p.z;
+  }
+  int np2 = 1;
+  while (np2 < c) np2 <<= 1;
+  __syncthreads();
+  for (int d = 0; d < SPH_NDIR; ++d) {
+    float ux, uy, uz;
+    dir_unit(d, ux, uy, uz);
+    if (t < np2) {
+      if (t < c) {
+        sk[t] = sort_key(px[t], py[t], pz[t], ux, uy, uz);
+        si[t] = f + t;
+      } else {
+        sk[t] = __int_as_float(0x7f800000);
+        si[t] = 0x7fffffff;
+      }
+    }
+    __syncthreads();
+    for (int k = 2; k <= np2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        if (t < np2) {
+          int p = t ^ j;
+          if (p > t) {
+            bool up = (t & k) == 0;
+            float ka = sk[t], kb = sk[p];
+            int ia = si[t], ib = si[p];
+            bool sw = up ? kv_less(kb, ib, ka, ia) : kv_less(ka, ia, kb, ib);
+            if (sw) {
+              sk[t] = kb; sk[p] = ka;
+              si[t] = ib; si[p] = ia;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (t < c) {
+      long long o = 13ll * f + (long long)d * c + t;
+      s_key[o] = sk[t];
+      s_idx[o] = si[t];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_need_pairs(int np, const int4* pairs, int* need) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= np) return;
+  int4 tk = pairs[t];
+  int ox, oy, oz, px, py, pz;
+  unpack_pair(tk.z, ox, oy, oz, px, py, pz);
+  int oc = off_code(ox, oy, oz);
+  int d = oc > 13 ? oc - 14 : 12 - oc;
+  atomicOr(&need[tk.x], 1 << d);
+  atomicOr(&need[tk.y], 1 << d);
+}
+
+__global__ void k_need_self(int ncell, const int* nblk, int* need) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id < ncell && nblk[id] > 1) atomicOr(&need[id], 1 << SPH_SELF_DIR);
+}
+
+__global__ void k_need_down(int g0, int g1, const int* child0, int* need) {
+  int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g1) return;
+  int c0 = child0[node], nd = need[node];
+  if (c0 < 0 || nd == 0) return;
+  for (int k = 0; k < 8; ++k) atomicOr(&need[c0 + k], nd);
+}
+
+__global__ void k_sort_size(int ncell, const int* need, const int* child0, const int* nblk,
+                            const int* count, long long* sz) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ncell) return;
+  bool alias = child0[id] < 0 && nblk[id] == 1;
+  sz[id] = (need[id] != 0 && !alias && count[id] > 0) ? 13ll * count[id] : 0;
+}
+
+__global__ void k_sort_base(int ncell, const int* need, const int* child0, const int* nblk,
+                            const int* first, const int* count, const long long* off,
+                            long long base, long long* sbase) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ncell) return;
+  bool alias = child0[id] < 0 && nblk[id] == 1;
+  if (alias) sbase[id] = 13ll * first[id];
+  else if (need[id] != 0 && count[id] > 0) sbase[id] = base + off[id];
+  else sbase[id] = -1;
+}
+
+constexpr int MERGE_MAXSUB = 256;
+
+__device__ __forceinline__ int count_less(const float* k, const int* ix, int n, float kv, int iv) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (kv_less(k[mid], ix[mid], kv, iv)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// CTA per node: merge the sub-lists (children, or the leaf's blocks) of
+// every needed direction by ranking each element in the other sub-lists
+__global__ void k_merge(int g0, int g1, const int* need, const int* child0, const int* count,
+                        const int* nblk, const int* blk0, const int* b_first, const int* b_count,
+                        const long long* sbase, float* s_key, int* s_idx, int* status) {
+  __shared__ long long sb[MERGE_MAXSUB];
+  __shared__ int sc[MERGE_MAXSUB];
+  __shared__ int spre[MERGE_MAXSUB + 1];
+  __shared__ int nsub;
+  int node = g0 + blockIdx.x;
+  if (node >= g1) return;
+  int nd = need[node];
+  bool leaf = child0[node] < 0;
+  if (nd == 0 || count[node] == 0 || (leaf && nblk[node] <= 1)) return;
+  int cnt = count[node];
+  long long ob = sbase[node];
+  for (int d = 0; d < SPH_NDIR; ++d) {
+    if (!((nd >> d) & 1)) continue;
+    if (threadIdx.x == 0) {
+      int ns = 0;
+      if (leaf) {
+        int nb = nblk[node];
+        if (nb > MERGE_MAXSUB) { atomicOr(status, ST_CAPACITY); nb = 0; }
+        for (int k = 0; k < nb; ++k) {
+          int bi = blk0[node] + k;
+          sb[ns] = 13ll * b_first[bi] + (long long)d * b_count[bi];
+          sc[ns] = b_count[bi];
+          ++ns;
+        }
+      } else {
+        for (int k = 0; k < 8; ++k) {
+          int ch = child0[node] + k;
+          int cc = count[ch];
+          if (cc == 0) continue;
+          sb[ns] = sbase[ch] + (long long)d * cc;
+          sc[ns] = cc;
+          ++ns;
+        }
+      }
+      spre[0] = 0;
+      for (int k = 0; k < ns; ++k) spre[k + 1] = spre[k] + sc[k];
+      nsub = ns;
+    }
+    __syncthreads();
+    int ns = nsub;
+    for (int e = threadIdx.x; e < spre[ns]; e += blockDim.x) {
+      int s = 0;
+      while (spre[s + 1] <= e) ++s;
+      int l = e - spre[s];
+      float kv = s_key[sb[s] + l];
+      int iv = s_idx[sb[s] + l];
+      int rank = l;
+      for (int o = 0; o < ns; ++o) {
+        if (o == s) continue;
+        rank += count_less(s_key + sb[o], s_idx + sb[o], sc[o], kv, iv);
+      }
+      long long dst = ob + (long long)d * cnt + rank;
+      s_key[dst] = kv;
+      s_idx[dst] = iv;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- interaction lists
+__global__ void k_pair_degree(int np, const int4* pairs, int* deg) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= np) return;
+  atomicAdd(&deg[pairs[t].x], 1);
+  atomicAdd(&deg[pairs[t].y], 1);
+}
+
+__global__ void k_pair_fill(int np, const int4* pairs, const int* off, int* cur, int* list) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= np) return;
+  int a = pairs[t].x, b = pairs[t].y;
+  list[off[a] + atomicAdd(&cur[a], 1)] = 2 * t;
+  list[off[b] + atomicAdd(&cur[b], 1)] = 2 * t + 1;
+}
+
+__global__ void k_pair_sortlists(int ncell, const int* off, const int* deg, int* list) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ncell) return;
+  int* l = list + off[id];
+  int n = deg[id];
+  for (int i = 1; i < n; ++i) {
+    int v = l[i], j = i - 1;
+    while (j >= 0 && l[j] > v) { l[j + 1] = l[j]; --j; }
+    l[j + 1] = v;
+  }
+}
+
+__global__ void k_block_ndt(int nblock, const int* b_leaf, const int* parent, const int* deg,
+                            long long* ndt) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblock) return;
+  long long c = 1;
+  for (int a = b_leaf[b]; a >= 0; a = parent[a]) c += deg[a];
+  ndt[b] = c;
+}
+
+__global__ void k_block_dts(int nblock, const int* b_leaf, const int* b_count, const int* parent,
+                            const int* deg, const int* aoff, const int* alist, const int4* pairs,
+                            const int* ntop, const int4* ijk, const int* box, const double* Ls,
+                            const int* box_t, const int* ncount, const long long* dtoff,
+                            int* dt_cj, int* dt_code, float4* dt_shift, unsigned long long* cost) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblock) return;
+  long long e = dtoff[b];
+  int leaf = b_leaf[b];
+  dt_cj[e] = leaf;
+  dt_code[e] = SPH_SELF_DIR | (1 << 8);
+  dt_shift[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  double c = (double)b_count[b] * (double)min(ncount[leaf], 4096);
+  ++e;
+  int bx = box[leaf];
+  double L = Ls[bx];
+  double et = L / (double)(1 << box_t[bx]);
+  int4 ta = ijk[ntop[leaf]];
+  for (int a = leaf; a >= 0; a = parent[a]) {
+    for (int k = 0; k < deg[a]; ++k) {
+      int v = alist[aoff[a] + k];
+      int4 tk = pairs[v >> 1];
+      int side = v & 1;
+      int ox, oy, oz, px, py, pz;
+      unpack_pair(tk.z, ox, oy, oz, px, py, pz);
+      int other = tk.y;
+      if (side) {
+        other = tk.x;
+        ox = -ox; oy = -oy; oz = -oz;
+        px = -px; py = -py; pz = -pz;
+      }
+      int oc = off_code(ox, oy, oz);
+      int dir, sgn;
+      if (oc > 13) { dir = oc - 14; sgn = 1; } else { dir = 12 - oc; sgn = -1; }
+      int4 tb = ijk[ntop[other]];
+      float sx = (float)((tb.x - ta.x) * et + px * L);
+      float sy = (float)((tb.y - ta.y) * et + py * L);
+      float sz = (float)((tb.z - ta.z) * et + pz * L);
+      dt_cj[e] = other;
+      dt_code[e] = dir | ((sgn + 1) << 8);
+      dt_shift[e] = make_float4(sx, sy, sz, 0.f);
+      c += (double)b_count[b] * (double)min(ncount[other], 4096) * 0.5;
+      ++e;
+    }
+  }
+  unsigned cc = c > 4.0e9 ? 0xffffffffu : (unsigned)c;
+  cost[b] = ((unsigned long long)(0xffffffffu - cc) << 32) | (unsigned)b;
+}
+
+__global__ void k_order_from_keys(int n, const unsigned long long* keys, int* order) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) order[i] = (int)(keys[i] & 0xffffffffu);
+}
+
+// warp per node: max of the current h over the node's particles
+__global__ void k_node_hmax(int ncell, const int* first, const int* count, const float* h,
+                            float* hmax) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= ncell) return;
+  int f = first[warp], c = count[warp];
+  float m = 0.f;
+  for (int k = lane; k < c; k += 32) m = fmaxf(m, h[f + k]);
+  m = warp_max(m);
+  if (lane == 0) hmax[warp] = m;
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side
+// ===========================================================================
+static int grow_copy(DBuf& b, size_t used, size_t want, cudaStream_t s) {
+  if (b.cap >= want) return SPH_OK;
+  DBuf nb;
+  SPH_TRY(dbuf_ensure(nb, want));
+  if (used > 0 && b.p) SPH_CUDA(cudaMemcpyAsync(nb.p, b.p, used, cudaMemcpyDeviceToDevice, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
+  dbuf_free(b);
+  b = nb;
+  return SPH_OK;
+}
+
+struct NodeBufs {
+  sph_ctx* c;
+  int grow(size_t used_nodes, size_t want_nodes, cudaStream_t s) {
+    DBuf* i4[] = {&c->n_first, &c->n_count, &c->n_parent, &c->n_child0, &c->n_top, &c->n_box};
+    for (DBuf* b : i4) SPH_TRY(grow_copy(*b, used_nodes * 4, want_nodes * 4, s));
+    SPH_TRY(grow_copy(c->n_ijk, used_nodes * 16, want_nodes * 16, s));
+    SPH_TRY(grow_copy(c->n_hbuild, used_nodes * 4, want_nodes * 4, s));
+    return SPH_OK;
+  }
+  NodeArrays arrays() {
+    NodeArrays na;
+    na.first = c->n_first.as<int>();
+    na.count = c->n_count.as<int>();
+    na.parent = c->n_parent.as<int>();
+    na.child0 = c->n_child0.as<int>();
+    na.top = c->n_top.as<int>();
+    na.box = c->n_box.as<int>();
+    na.ijk = c->n_ijk.as<int4>();
+    na.hbuild = c->n_hbuild.as<float>();
+    return na;
+  }
+};
+
+template <class T>
+static int d2h(T* dst, const void* src, cudaStream_t s) {
+  SPH_CUDA(cudaMemcpyAsync(dst, src, sizeof(T), cudaMemcpyDeviceToHost, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
+  return SPH_OK;
+}
+
+// Octree over the Morton-sorted particles (mode 0: Section 3.2 split rule
+// on the h in c->hguess; mode 1: count-only split for the h estimate).
+static int build_tree(sph_ctx* c, int mode, cudaStream_t s) {
+  const int n = (int)c->n;
+  const int K = c->kbits;
+  // top grid
+  c->top_base.assign(c->nbox + 1, 0);
+  for (int b = 0; b < c->nbox; ++b) {
+    long long nb = 1ll << c->box_t[b];
+    c->top_base[b + 1] = c->top_base[b] + (int)(nb * nb * nb);
+  }
+  c->ntop = c->top_base[c->nbox];
+  SPH_CUDA(cudaMemcpyAsync(c->d_top_base.p, c->top_base.data(), sizeof(int) * (c->nbox + 1),
+                           cudaMemcpyHostToDevice, s));
+  SPH_CUDA(cudaMemcpyAsync(c->d_box_t.p, c->box_t.data(), sizeof(int) * c->nbox,
+                           cudaMemcpyHostToDevice, s));
+  NodeBufs nbufs{c};
+  size_t cap0 = (size_t)c->ntop + 8 * ((size_t)n / 64 + 16);
+  SPH_TRY(nbufs.grow(0, cap0, s));
+  NodeArrays na = nbufs.arrays();
+  { k_init_top<<<div_up(c->ntop, TPB), TPB, 0, s>>>(c->ntop, c->d_top_base.as<int>(),
+                                                  c->d_box_t.as<int>(), c->nbox,
+                                                  c->keys.as<unsigned long long>(), n, K, na); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  c->gen_start.assign(1, 0);
+  c->gen_start.push_back(c->ntop);
+  int g0 = 0, g1 = c->ntop;
+  int maxd = 0;
+  for (int b = 0; b < c->nbox; ++b) maxd = std::max(maxd, c->box_t[b]);
+  for (;;) {
+    int ng = g1 - g0;
+    SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (ng + 1)));
+    SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (ng + 1)));
+    na = nbufs.arrays();
+    { k_node_stats<<<div_up((long long)ng * 32, TPB), TPB, 0, s>>>(
+        g0, g1, mode, c->prm.split_count, c->prm.split_frac, K, c->hguess.as<float>(),
+        c->d_box_L.as<double>(), na, c->t_cnt.as<int>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    SPH_TRY(scan_exclusive_i32(c->t_cnt.as<int>(), c->t_off.as<int>(), ng,
+                               c->t_off.as<int>() + ng, c->scan_tmp, s));
+    int nsplit = 0;
+    SPH_TRY(d2h(&nsplit, c->t_off.as<int>() + ng, s));
+    if (nsplit == 0) break;
+    SPH_TRY(nbufs.grow((size_t)g1, (size_t)g1 + 8 * (size_t)nsplit, s));
+    na = nbufs.arrays();
+    { k_make_children<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, g1, c->t_cnt.as<int>(),
+                                                    c->t_off.as<int>(),
+                                                    c->keys.as<unsigned long long>(), K, na); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    g0 = g1;
+    g1 += 8 * nsplit;
+    c->gen_start.push_back(g1);
+    ++maxd;
+  }
+  c->ncell = g1;
+  c->max_depth = maxd;
+  SPH_TRY(dbuf_ensure(c->pnode, sizeof(int) * (size_t)n));
+  { k_leaf_particles<<<div_up((long long)c->ncell * 32, TPB), TPB, 0, s>>>(
+      c->ncell, c->n_first.as<int>(), c->n_count.as<int>(), c->n_child0.as<int>(),
+      c->pnode.as<int>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+static int choose_top_levels(sph_ctx* c, cudaStream_t s) {
+  // per-box max of the build h (host reduction over a D2H copy of per-box maxima)
+  const int n = (int)c->n;
+  std::vector<float> hmax(c->nbox, 0.f);
+  {
+    // small kernel-free approach: copy h to host in chunks is too slow for large n;
+    // reuse k_node_hmax over pseudo-nodes = boxes
+    SPH_TRY(dbuf_ensure(c->tmp_a, sizeof(int) * c->nbox * 2 + 64));
+    SPH_TRY(dbuf_ensure(c->tmp_b, sizeof(float) * c->nbox + 64));
+    std::vector<int> fc(2 * c->nbox);
+    for (int b = 0; b < c->nbox; ++b) {
+      fc[b] = (int)c->box_off[b];
+      fc[c->nbox + b] = (int)(c->box_off[b + 1] - c->box_off[b]);
+    }
+    SPH_CUDA(cudaMemcpyAsync(c->tmp_a.p, fc.data(), sizeof(int) * 2 * c->nbox,
+                             cudaMemcpyHostToDevice, s));
+    { k_node_hmax<<<div_up((long long)c->nbox * 32, TPB), TPB, 0, s>>>(
+        c->nbox, c->tmp_a.as<int>(), c->tmp_a.as<int>() + c->nbox, c->hguess.as<float>(),
+        c->tmp_b.as<float>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    SPH_CUDA(cudaMemcpyAsync(hmax.data(), c->tmp_b.p, sizeof(float) * c->nbox,
+                             cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+  }
+  (void)n;
+  c->box_t.assign(c->nbox, 2);
+  for (int b = 0; b < c->nbox; ++b) {
+    double L = c->box_L[b];
+    double hm = hmax[b];
+    if (!(hm > 0) || !std::isfinite(hm)) return SPH_ERR_INVALID_ARG;
+    if (hm > L / 4.0) return SPH_ERR_INVALID_ARG;
+    int t = (int)std::floor(std::log2(L / hm));
+    while (t > 2 && L / (double)(1ll << t) < hm) --t;
+    t = std::min(t, 7);
+    t = std::min(t, c->kbits);
+    t = std::max(t, 2);
+    c->box_t[b] = t;
+  }
+  return SPH_OK;
+}
+
+int compute_node_hmax(sph_ctx* c, cudaStream_t s) {
+  SPH_TRY(dbuf_ensure(c->n_hmax, sizeof(float) * (size_t)c->ncell));
+  { k_node_hmax<<<div_up((long long)c->ncell * 32, TPB), TPB, 0, s>>>(
+      c->ncell, c->n_first.as<int>(), c->n_count.as<int>(), c->h.as<float>(),
+      c->n_hmax.as<float>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+static int build_tasks(sph_ctx* c, cudaStream_t s) {
+  const int ncell = c->ncell;
+  // psplit flags (n_flags) cleared
+  SPH_TRY(dbuf_ensure(c->n_flags, sizeof(int) * ncell));
+  SPH_CUDA(cudaMemsetAsync(c->n_flags.p, 0, sizeof(int) * ncell, s));
+  // generation 0: top cells
+  int ntop = c->ntop;
+  SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (ntop + 1)));
+  SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (ntop + 1)));
+  { k_top_tasks<<<div_up(ntop, TPB), TPB, 0, s>>>(ntop, c->d_top_base.as<int>(),
+                                                c->d_box_t.as<int>(), c->nbox,
+                                                c->n_count.as<int>(), nullptr,
+                                                c->t_cnt.as<int>(), nullptr); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(scan_exclusive_i32(c->t_cnt.as<int>(), c->t_off.as<int>(), ntop,
+                             c->t_off.as<int>() + ntop, c->scan_tmp, s));
+  int nt = 0;
+  SPH_TRY(d2h(&nt, c->t_off.as<int>() + ntop, s));
+  SPH_TRY(dbuf_ensure(c->t_cur, sizeof(int4) * (size_t)(nt + 1)));
+  { k_top_tasks<<<div_up(ntop, TPB), TPB, 0, s>>>(ntop, c->d_top_base.as<int>(),
+                                                c->d_box_t.as<int>(), c->nbox,
+                                                c->n_count.as<int>(), c->t_off.as<int>(),
+                                                nullptr, c->t_cur.as<int4>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  int nfs_total = 0, nfp_total = 0;
+  size_t fs_cap = 0, fp_cap = 0;
+  DBuf fs_buf, fp_buf;
+  while (nt > 0) {
+    SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * 3 * (size_t)(nt + 1)));
+    SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * 3 * (size_t)(nt + 1)));
+    int* nch = c->t_cnt.as<int>();
+    int* nfs = nch + (nt + 1);
+    int* nfp = nfs + (nt + 1);
+    int* och = c->t_off.as<int>();
+    int* ofs = och + (nt + 1);
+    int* ofp = ofs + (nt + 1);
+    { k_refine<<<div_up(nt, TPB), TPB, 0, s>>>(
+        nt, c->t_cur.as<int4>(), c->n_child0.as<int>(), c->n_count.as<int>(),
+        c->n_hbuild.as<float>(), c->n_ijk.as<int4>(), c->n_box.as<int>(), c->d_box_L.as<double>(),
+        nch, nfs, nfp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    SPH_TRY(scan_exclusive_i32(nch, och, nt, och + nt, c->scan_tmp, s));
+    SPH_TRY(scan_exclusive_i32(nfs, ofs, nt, ofs + nt, c->scan_tmp, s));
+    SPH_TRY(scan_exclusive_i32(nfp, ofp, nt, ofp + nt, c->scan_tmp, s));
+    int tot[3];
+    SPH_TRY(d2h(&tot[0], och + nt, s));
+    SPH_TRY(d2h(&tot[1], ofs + nt, s));
+    SPH_TRY(d2h(&tot[2], ofp + nt, s));
+    SPH_TRY(dbuf_ensure(c->t_next, sizeof(int4) * (size_t)(tot[0] + 1)));
+    if ((size_t)(nfs_total + tot[1]) > fs_cap) {
+      fs_cap = (size_t)(nfs_total + tot[1]) * 2 + 1024;
+      SPH_TRY(grow_copy(fs_buf, sizeof(int) * nfs_total, sizeof(int) * fs_cap, s));
+    }
+    if ((size_t)(nfp_total + tot[2]) > fp_cap) {
+      fp_cap = (size_t)(nfp_total + tot[2]) * 2 + 1024;
+      SPH_TRY(grow_copy(fp_buf, sizeof(int4) * nfp_total, sizeof(int4) * fp_cap, s));
+    }
+    { k_refine<<<div_up(nt, TPB), TPB, 0, s>>>(
+        nt, c->t_cur.as<int4>(), c->n_child0.as<int>(), c->n_count.as<int>(),
+        c->n_hbuild.as<float>(), c->n_ijk.as<int4>(), c->n_box.as<int>(), c->d_box_L.as<double>(),
+        nullptr, nullptr, nullptr, och, ofs, ofp, c->t_next.as<int4>(), fs_buf.as<int>(),
+        fp_buf.as<int4>(), nfs_total, nfp_total, c->n_flags.as<int>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    nfs_total += tot[1];
+    nfp_total += tot[2];
+    std::swap(c->t_cur, c->t_next);
+    nt = tot[0];
+  }
+  dbuf_free(c->t_final_self);
+  dbuf_free(c->t_final_pair);
+  c->t_final_self = fs_buf;
+  c->t_final_pair = fp_buf;
+  c->nself = nfs_total;
+  c->npair = nfp_total;
+  // cell limits
+  SPH_TRY(dbuf_ensure(c->n_hlim, sizeof(float) * ncell));
+  for (size_t g = 0; g + 1 < c->gen_start.size(); ++g) {
+    int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
+    { k_hlim<<<div_up(g1 - g0, TPB), TPB, 0, s>>>(g0, g1, c->n_parent.as<int>(),
+                                                c->n_flags.as<int>(), c->n_ijk.as<int4>(),
+                                                c->n_box.as<int>(), c->d_box_L.as<double>(),
+                                                c->n_hlim.as<float>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  SPH_TRY(dbuf_ensure(c->hlim, sizeof(float) * (size_t)c->n));
+  { k_particle_hlim<<<div_up(c->n, TPB), TPB, 0, s>>>(c->n, c->pnode.as<int>(),
+                                                    c->n_hlim.as<float>(), c->hlim.as<float>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
+  const int ncell = c->ncell;
+  const long long n = c->n;
+  // blocks
+  SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->tmp_c, sizeof(int) * (ncell + 1)));  // nblk per node (kept)
+  int* nblk = c->tmp_c.as<int>();
+  { k_leaf_nblk<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, c->n_child0.as<int>(),
+                                                 c->n_count.as<int>(), c->prm.block_max, nblk); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(scan_exclusive_i32(nblk, c->t_off.as<int>(), ncell, c->t_off.as<int>() + ncell,
+                             c->scan_tmp, s));
+  int nblock = 0;
+  SPH_TRY(d2h(&nblock, c->t_off.as<int>() + ncell, s));
+  c->nblock = nblock;
+  SPH_TRY(dbuf_ensure(c->b_first, sizeof(int) * (nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->b_count, sizeof(int) * (nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->b_leaf, sizeof(int) * (nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->n_need, sizeof(int) * (ncell + 1)));  // reused below as need
+  SPH_TRY(dbuf_ensure(c->adj_off, sizeof(int) * (ncell + 1)));  // temporarily blk0
+  DBuf blk0_buf;
+  SPH_TRY(dbuf_ensure(blk0_buf, sizeof(int) * (ncell + 1)));
+  { k_make_blocks<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, c->n_first.as<int>(),
+                                                   c->n_count.as<int>(), nblk, c->t_off.as<int>(),
+                                                   c->b_first.as<int>(), c->b_count.as<int>(),
+                                                   c->b_leaf.as<int>(), blk0_buf.as<int>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  // block sorts: lists of all 13 directions at [13 first, 13 (first + count))
+  // needs
+  int* need = c->n_need.as<int>();
+  SPH_CUDA(cudaMemsetAsync(need, 0, sizeof(int) * ncell, s));
+  if (c->npair > 0) {
+    { k_need_pairs<<<div_up(c->npair, TPB), TPB, 0, s>>>(c->npair, c->t_final_pair.as<int4>(), need); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  { k_need_self<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, nblk, need); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  for (size_t g = 0; g + 1 < c->gen_start.size(); ++g) {
+    int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
+    { k_need_down<<<div_up(g1 - g0, TPB), TPB, 0, s>>>(g0, g1, c->n_child0.as<int>(), need); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  DBuf sz;
+  SPH_TRY(dbuf_ensure(sz, sizeof(long long) * (ncell + 1) * 2));
+  long long* szp = sz.as<long long>();
+  long long* szo = szp + (ncell + 1);
+  { k_sort_size<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, need, c->n_child0.as<int>(), nblk,
+                                                 c->n_count.as<int>(), szp); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(scan_exclusive_i64(szp, szo, ncell, szo + ncell, c->scan_tmp, s));
+  long long extra = 0;
+  SPH_TRY(d2h(&extra, szo + ncell, s));
+  c->sorted_entries = 13ll * n + extra;
+  SPH_TRY(dbuf_ensure(c->s_key, sizeof(float) * (size_t)c->sorted_entries));
+  SPH_TRY(dbuf_ensure(c->s_idx, sizeof(int) * (size_t)c->sorted_entries));
+  SPH_TRY(dbuf_ensure(c->n_sbase, sizeof(long long) * (ncell + 1)));
+  { k_sort_base<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, need, c->n_child0.as<int>(), nblk,
+                                                 c->n_first.as<int>(), c->n_count.as<int>(), szo,
+                                                 13ll * n, c->n_sbase.as<long long>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  if (nblock > 0) {
+    { k_sort_blocks<<<nblock, SORT_MAX, 0, s>>>(c->b_first.as<int>(), c->b_count.as<int>(),
+                                              c->pos4.as<float4>(), c->s_key.as<float>(),
+                                              c->s_idx.as<int>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  for (int g = (int)c->gen_start.size() - 2; g >= 0; --g) {
+    int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
+    if (g1 <= g0) continue;
+    { k_merge<<<g1 - g0, 256, 0, s>>>(g0, g1, need, c->n_child0.as<int>(), c->n_count.as<int>(),
+                                    nblk, blk0_buf.as<int>(), c->b_first.as<int>(),
+                                    c->b_count.as<int>(), c->n_sbase.as<long long>(),
+                                    c->s_key.as<float>(), c->s_idx.as<int>(),
+                                    c->status.as<int>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  dbuf_free(sz);
+  dbuf_free(blk0_buf);
+
+  // ---- interaction lists per block
+  int* deg = c->t_cnt.as<int>();
+  int* aoff = c->adj_off.as<int>();
+  SPH_CUDA(cudaMemsetAsync(deg, 0, sizeof(int) * (ncell + 1), s));
+  if (c->npair > 0) {
+    { k_pair_degree<<<div_up(c->npair, TPB), TPB, 0, s>>>(c->npair, c->t_final_pair.as<int4>(), deg); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  SPH_TRY(scan_exclusive_i32(deg, aoff, ncell, aoff + ncell, c->scan_tmp, s));
+  SPH_TRY(dbuf_ensure(c->adj_list, sizeof(int) * (size_t)(2 * c->npair + 1)));
+  SPH_TRY(dbuf_ensure(c->t_cnt2, sizeof(int) * (ncell + 1)));
+  SPH_CUDA(cudaMemsetAsync(c->t_cnt2.p, 0, sizeof(int) * (ncell + 1), s));
+  if (c->npair > 0) {
+    { k_pair_fill<<<div_up(c->npair, TPB), TPB, 0, s>>>(c->npair, c->t_final_pair.as<int4>(), aoff,
+                                                     c->t_cnt2.as<int>(), c->adj_list.as<int>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  { k_pair_sortlists<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, aoff, deg, c->adj_list.as<int>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(dbuf_ensure(c->b_dtoff, sizeof(long long) * (nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->tmp_b, sizeof(long long) * (nblock + 1)));
+  { k_block_ndt<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, c->b_leaf.as<int>(),
+                                                  c->n_parent.as<int>(), deg,
+                                                  c->tmp_b.as<long long>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(scan_exclusive_i64(c->tmp_b.as<long long>(), c->b_dtoff.as<long long>(), nblock,
+                             c->b_dtoff.as<long long>() + nblock, c->scan_tmp, s));
+  long long ndt = 0;
+  SPH_TRY(d2h(&ndt, c->b_dtoff.as<long long>() + nblock, s));
+  c->ndt = ndt;
+  SPH_TRY(dbuf_ensure(c->dt_cj, sizeof(int) * (size_t)(ndt + 1)));
+  SPH_TRY(dbuf_ensure(c->dt_code, sizeof(int) * (size_t)(ndt + 1)));
+  SPH_TRY(dbuf_ensure(c->dt_shift, sizeof(float4) * (size_t)(ndt + 1)));
+  SPH_TRY(dbuf_ensure(c->b_cost, sizeof(unsigned long long) * (nblock + 1) * 2));
+  SPH_TRY(dbuf_ensure(c->b_order, sizeof(int) * (nblock + 1) * 2));
+  unsigned long long* ck = c->b_cost.as<unsigned long long>();
+  { k_block_dts<<<div_up(nblock, TPB), TPB, 0, s>>>(
+      nblock, c->b_leaf.as<int>(), c->b_count.as<int>(), c->n_parent.as<int>(), deg, aoff,
+      c->adj_list.as<int>(), c->t_final_pair.as<int4>(), c->n_top.as<int>(), c->n_ijk.as<int4>(),
+      c->n_box.as<int>(), c->d_box_L.as<double>(), c->d_box_t.as<int>(), c->n_count.as<int>(),
+      c->b_dtoff.as<long long>(), c->dt_cj.as<int>(), c->dt_code.as<int>(),
+      c->dt_shift.as<float4>(), ck); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  // LPT order: descending cost, ties by block id
+  int* ov = c->b_order.as<int>();
+  { k_order_from_keys<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, ck, ov); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(radix_sort_u64(ck, ov, ck + (nblock + 1), ov + (nblock + 1), nblock, 64, c->sort_tmp, s));
+  { k_order_from_keys<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, ck, ov); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  // count leaves (host copy of nblk not needed: leaves = nodes with nblk > 0)
+  {
+    std::vector<int> hb(ncell);
+    SPH_CUDA(cudaMemcpyAsync(hb.data(), nblk, sizeof(int) * ncell, cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+    int nl = 0;
+    for (int v : hb) nl += v > 0;
+    c->nleaf = nl;
+  }
+  return SPH_OK;
+}
+
+int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cudaStream_t s) {
+  const long long n = c->n;
+  const int K = c->kbits;
+  int boxbits = 0;
+  while ((1 << boxbits) < c->nbox) ++boxbits;
+  SPH_TRY(dbuf_ensure(c->keys, 8 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->keys_alt, 8 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->perm, 4 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->perm_alt, 4 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->xs, 24 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->hguess, 4 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->h, 4 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->pos4, 16 * (size_t)n));
+  { k_keys<<<div_up(n, TPB), TPB, 0, s>>>(pos, n, c->d_box_off.as<long long>(),
+                                        c->d_box_L.as<double>(), c->nbox, K,
+                                        c->keys.as<unsigned long long>(), c->perm.as<int>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(radix_sort_u64(c->keys.as<unsigned long long>(), c->perm.as<int>(),
+                         c->keys_alt.as<unsigned long long>(), c->perm_alt.as<int>(), (int)n,
+                         3 * K + boxbits, c->sort_tmp, s));
+  { k_gather_pos<<<div_up(n, TPB), TPB, 0, s>>>(pos, c->perm.as<int>(), n,
+                                              c->d_box_off.as<long long>(),
+                                              c->d_box_L.as<double>(), c->nbox, h_guess,
+                                              c->xs.as<double>(), c->hguess.as<float>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  if (!h_guess) {
+    // count-only octree below a 4^3 top grid gives a local-density h estimate
+    c->box_t.assign(c->nbox, 2);
+    SPH_TRY(build_tree(c, 1, s));
+    { k_h_estimate<<<div_up(n, TPB), TPB, 0, s>>>(n, c->pnode.as<int>(), c->n_parent.as<int>(),
+                                                c->n_count.as<int>(), c->n_ijk.as<int4>(),
+                                                c->n_box.as<int>(), c->d_box_L.as<double>(),
+                                                c->prm.n_ngb, c->hguess.as<float>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  return build_from_guess(c, s);
+}
+
+int build_from_guess(sph_ctx* c, cudaStream_t s) {
+  const long long n = c->n;
+  SPH_TRY(choose_top_levels(c, s));
+  SPH_TRY(build_tree(c, 0, s));
+  { k_relpos<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), c->xs.as<double>(),
+                                          c->d_box_L.as<double>(), c->d_box_t.as<int>(), c->kbits,
+                                          c->pos4.as<float4>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(build_tasks(c, s));
+  SPH_TRY(build_blocks_and_sorts(c, s));
+  SPH_CUDA(cudaMemcpyAsync(c->h.p, c->hguess.p, sizeof(float) * (size_t)n,
+                           cudaMemcpyDeviceToDevice, s));
+  SPH_TRY(compute_node_hmax(c, s));
+  return SPH_OK;
+}

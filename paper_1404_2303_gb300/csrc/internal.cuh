@@ -1,0 +1,194 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "sphgb.h"
+
+#define SPH_MAX_BOX 1024
+#define SPH_NDIR 13
+#define SPH_SELF_DIR 0  // self interactions sweep along sort direction 0 (the z axis)
+
+// ---------------------------------------------------------------------------
+// error handling: every CUDA call is checked and mapped to SPH_ERR_CUDA
+// ---------------------------------------------------------------------------
+#define SPH_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      fprintf(stderr, "sphgb: %s failed at %s:%d: %s\n", #call, __FILE__, __LINE__,     \
+              cudaGetErrorString(e_));                                                   \
+      return e_ == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA;               \
+    }                                                                                    \
+  } while (0)
+
+#define SPH_TRY(expr)        \
+  do {                       \
+    int r_ = (expr);         \
+    if (r_ != SPH_OK) return r_; \
+  } while (0)
+
+// device status word bits
+enum : int {
+  ST_CELL_LIMIT = 1,
+  ST_NOT_CONVERGED = 2,
+  ST_CAPACITY = 4,
+  ST_BAD_INDEX = 8,
+  ST_TIMEOUT = 16,
+};
+
+// ---------------------------------------------------------------------------
+// device buffers owned by the context
+// ---------------------------------------------------------------------------
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+int dbuf_ensure(DBuf& b, size_t bytes);
+void dbuf_free(DBuf& b);
+
+// ---------------------------------------------------------------------------
+// primitives (prims.cu)
+// ---------------------------------------------------------------------------
+// exclusive scans; `total` (device, nullable) receives the sum
+int scan_exclusive_i32(const int* in, int* out, int n, int* total, DBuf& tmp, cudaStream_t s);
+int scan_exclusive_i64(const long long* in, long long* out, int n, long long* total, DBuf& tmp,
+                       cudaStream_t s);
+// stable LSD radix sort of (key, value) on bits [0, nbits) of the keys.
+// Sorted data ends in keys/vals; keys_alt/vals_alt are scratch of size n.
+int radix_sort_u64(unsigned long long* keys, int* vals, unsigned long long* keys_alt, int* vals_alt,
+                   int n, int nbits, DBuf& tmp, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// the context
+// ---------------------------------------------------------------------------
+struct sph_ctx {
+  sph_params prm;
+  // problem
+  int64_t n = 0;
+  int nbox = 0;
+  int kbits = 16;  // morton bits per axis
+  std::vector<long long> box_off;  // nbox+1
+  std::vector<double> box_L;       // nbox
+  std::vector<int> box_t;          // log2 top cells per axis
+  std::vector<int> top_base;       // first top-cell node per box (nbox+1)
+  bool built = false;
+  bool have_density = false;
+  bool have_force = false;
+  int have_d2 = 0;
+
+  // box tables (device)
+  DBuf d_box_off, d_box_L, d_box_t, d_top_base;
+
+  // particles in Morton (cell) order
+  DBuf keys, keys_alt, perm, perm_alt;
+  DBuf xs;        // double, 3 per particle (wrapped absolute positions)
+  DBuf pos4;      // float4 (x_rel, y_rel, z_rel, m)
+  DBuf h;         // float current smoothing length
+  DBuf hguess;    // float build-time h
+  DBuf hlim;      // float per-particle cell limit
+  DBuf pnode;     // int leaf node of each particle
+
+  // octree nodes
+  int ncell = 0, ntop = 0, max_depth = 0;
+  std::vector<int> gen_start;  // node id where each generation starts (+ end)
+  DBuf n_first, n_count, n_parent, n_child0, n_top, n_flags, n_need;
+  DBuf n_ijk;     // int4 (ix, iy, iz, level)
+  DBuf n_box;     // int
+  DBuf n_hmax;    // float max h of the particles in the node (current h)
+  DBuf n_hbuild;  // float max h at build time
+  DBuf n_hlim;    // float
+  DBuf n_sbase;   // long long: base of the node's 13 sorted lists (-1 none)
+
+  // tasks
+  int nself = 0, npair = 0;
+  DBuf t_cur, t_next;        // int4 work tasks per generation
+  DBuf t_final_pair;         // int4 {ci, cj, packed offset/periodic, 0}
+  DBuf t_final_self;         // int
+  DBuf t_cnt, t_cnt2, t_off, t_off2;
+
+  // blocks
+  int nblock = 0, nleaf = 0;
+  int64_t ndt = 0;
+  DBuf b_first, b_count, b_leaf, b_dtoff, b_order, b_cost;
+  DBuf dt_cj;      // int
+  DBuf dt_code;    // int: dir | (sgn+1) << 8
+  DBuf dt_shift;   // float4 (sx, sy, sz, 0)
+  DBuf adj_off, adj_list;  // per-node CSR of final pair tasks
+
+  // sorted lists
+  int64_t sorted_entries = 0;
+  DBuf s_key, s_idx;
+
+  // physics state (cell order)
+  DBuf rho, drho, nngb, dnngb, d2rho, omega, Avec, fdat;  // fdat: float4 per particle for force
+  DBuf vel4;      // float4 (vx, vy, vz, hinv)
+  DBuf u_s;       // float
+  DBuf acc4;      // float4 (ax, ay, az, dudt)
+  DBuf cnt_i;     // int per-particle counts
+  // h solver
+  DBuf h_lo, h_hi;   // double bracket
+  DBuf h_flag;       // int: bit0 active, bit1 hi evaluated, bit2 cell limit
+  DBuf blk_active;   // int per block
+  // adjoint state
+  DBuf adj4, adj4b;  // adjoint per-particle j data (cell order)
+  DBuf g_A, g_rho_s, g_drho_s, g_h_s, g_u_s, g_x4;
+
+  // misc
+  DBuf status;       // int device status word + counters
+  DBuf counters;     // long long[8]
+  DBuf queue;        // int work counters
+  DBuf scan_tmp, sort_tmp, tmp_a, tmp_b, tmp_c;
+  int* dump_pi = nullptr;
+  int* dump_pj = nullptr;
+  long long dump_cap = 0;
+
+  sph_stats stats{};
+  int sweep_grid = 0;
+  int sweep_threads = 0;
+  // profiling: (phase, start, stop) events recorded around sweep launches
+  bool profile = false;
+  int cur_phase = 0;
+  struct Ev { int phase; cudaEvent_t a, b; };
+  std::vector<Ev> ev_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  DBuf prof_units;  // unsigned long long per pending profiled launch
+  unsigned long long prof_units_acc[8] = {0};
+  double prof_ms[8] = {0};
+  int prof_n[8] = {0};
+};
+cudaEvent_t ev_get(sph_ctx* c);
+int prof_resolve(sph_ctx* c);
+
+// ---------------------------------------------------------------------------
+// stages (build.cu, sweep.cu)
+// ---------------------------------------------------------------------------
+int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cudaStream_t s);
+// rebuild cells, tasks, blocks and sorted lists from the h in c->hguess
+// (Morton order and positions unchanged)
+int build_from_guess(sph_ctx* c, cudaStream_t s);
+int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t s);
+int compute_node_hmax(sph_ctx* c, cudaStream_t s);
+
+// sweep phases
+enum : int {
+  PH_DENSITY = 0,      // rho, drho/dh, N, dN/dh (+count)
+  PH_DENSITY_D2 = 1,   // d^2 rho/dh^2 only
+  PH_FORCE = 2,        // acc, du/dt (+count)
+  PH_FORCE_ADJ = 3,    // force adjoint gather
+  PH_DENSITY_ADJ = 4,  // density adjoint gather
+  PH_DUMP_DENSITY = 5,
+  PH_DUMP_FORCE = 6,
+};
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// running count of kernel launches issued by this library (all contexts)
+void note_launch();
+long long launch_count();

@@ -1,0 +1,767 @@
+// Interaction sweeps: the sorted cell-pair interactions of Section 3.3 run
+// as persistent warps.  A warp owns one particle block (a leaf cell or a
+// slice of a large leaf) and walks the block's directed interaction list:
+// its own leaf (the self interaction, swept inside a two-sided window along
+// one axis) and every cell it shares a final pair task with (the pair
+// interaction, swept from the interface along the 13-direction sort axis
+// with the axial cutoff of the paper's sorted loop).  Each particle's sums
+// stay with the warp that owns it, so no atomics touch the accumulators;
+// each pair is evaluated from both sides instead of being updated
+// symmetrically under the task conflicts of Section 3.4.
+//
+// Per chunk of 32 i-particles (consecutive in the block's sorted order, so
+// their axial windows nearly coincide) the j-particles inside the chunk's
+// window are staged 32 at a time in shared memory and every lane evaluates
+// every staged j (branch-free: the cubic spline's clamps zero everything
+// beyond the support).
+#include <algorithm>
+#include <cfloat>
+
+#include "geom.cuh"
+#include "internal.cuh"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr float SIGMA = 2.546479089470325f;  // 8/pi
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// first index in the ascending keys[0, n) with keys[i] >= v (warp-wide)
+__device__ __forceinline__ int warp_lower_bound(const float* keys, int n, float v) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = n;
+  while (hi - lo > 32) {
+    int step = (hi - lo + 31) >> 5;
+    int pos = lo + lane * step;
+    bool less = pos < hi && keys[pos] < v;
+    int c = __popc(__ballot_sync(FULL, less));
+    int nlo = c > 0 ? lo + (c - 1) * step + 1 : lo;
+    int nhi = min(hi, lo + c * step);
+    lo = nlo;
+    hi = nhi;
+  }
+  int pos = lo + lane;
+  bool less = pos < hi && keys[pos] < v;
+  return lo + __popc(__ballot_sync(FULL, less));
+}
+
+struct SweepArgs {
+  int nblock;
+  const int* order;
+  const int* b_first;
+  const int* b_count;
+  const long long* b_dtoff;
+  const int* dt_cj;
+  const int* dt_code;
+  const float4* dt_shift;
+  const int* n_count;
+  const long long* n_sbase;
+  const float* n_hmax;
+  const float* s_key;
+  const int* s_idx;
+  const float4* pos4;   // x_rel, y_rel, z_rel, m
+  const float* h;
+  const float4* vel4;   // vx, vy, vz, 1/h
+  const float4* fdat;   // force: (D = 6 sigma m A / h^4, h^2, C = 6 sigma A / h^4, A)
+  const float4* adj4;   // adjoint j data
+  const float4* adj4b;
+  const int* blk_active;
+  int* queue;
+  int* status;
+  float delta;
+  int kahan;
+  int bmax;
+  // outputs (cell order)
+  float* o0;
+  float* o1;
+  float* o2;
+  float* o3;
+  float4* o4;
+  float4* o5;
+  int* ocnt;
+  unsigned long long* units;  // profiling: accepted pairs of this launch
+  // pair dump
+  const int* perm;
+  int* dump_i;
+  int* dump_j;
+  unsigned long long* dump_n;
+  long long dump_cap;
+};
+
+// ---------------------------------------------------------------------------
+// density, Eq. (rho) and Eq. (nneigh): per directed interaction (i <- j),
+// with w = 2 (a^3 - 4 b^3), w' = 6 (4 b^2 - a^2), a = (1-q)+, b = (1/2-q)+,
+// accumulate  m w/2,  m (w/2 + q w'/6),  w/2,  q w'/6
+// ---------------------------------------------------------------------------
+struct PDensity {
+  static constexpr int NACC = 4;
+  static constexpr int JW = 1;
+  static constexpr bool USES_HJ = false;
+  struct I {
+    float x, y, z, h, hinv, h2;
+  };
+  __device__ static void load_i(const SweepArgs& a, int p, I& i) {
+    float4 q = a.pos4[p];
+    float h = a.h[p];
+    i.x = q.x; i.y = q.y; i.z = q.z;
+    i.h = h;
+    i.hinv = 1.0f / h;
+    i.h2 = __fmul_rn(h, h);
+  }
+  __device__ static void null_i(I& i) {
+    i.x = i.y = i.z = 0.f;
+    i.h = 0.f; i.hinv = 0.f; i.h2 = 0.f;
+  }
+  __device__ static float cut(const I& i, float) { return i.h; }
+  __device__ static float maxcut(float hb, float) { return hb; }
+  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
+    float4 q = a.pos4[j];
+    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
+  }
+  template <bool COUNT>
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+    float4 p = tile[t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    float q = sqrt_approx(r2) * i.hinv;
+    float aa = fmaxf(1.f - q, 0.f), bb = fmaxf(0.5f - q, 0.f);
+    float a2 = aa * aa, b2 = bb * bb;
+    float wh = fmaf(-4.f * b2, bb, a2 * aa);  // w/2
+    float d6 = fmaf(4.f, b2, -a2);            // w'/6
+    float qd = q * d6;
+    acc[0] = fmaf(p.w, wh, acc[0]);
+    acc[1] = fmaf(p.w, wh + qd, acc[1]);
+    acc[2] += wh;
+    acc[3] += qd;
+    if (COUNT) cnt += r2 < i.h2 ? 1 : 0;
+  }
+  // rho = sigma/h^3 * 2 S0; drho/dh = -sigma/h^4 * 6 S1; N = 64/3 S2; dN/dh = -64/h S3
+  __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
+    float h = a.h[p];
+    float hi = 1.0f / h;
+    float hi3 = hi * hi * hi;
+    a.o0[p] = 2.f * SIGMA * hi3 * s[0];
+    if (a.o1) a.o1[p] = -6.f * SIGMA * hi3 * hi * s[1];
+    if (a.o2) a.o2[p] = (64.f / 3.f) * s[2];
+    if (a.o3) a.o3[p] = -64.f * hi * s[3];
+  }
+};
+
+// d^2 rho / dh^2 = sigma/h^5 sum m (12 w + 8 q w' + q^2 w''), w'' = 12 (a - 4b)
+struct PDensityD2 {
+  static constexpr int NACC = 1;
+  static constexpr int JW = 1;
+  static constexpr bool USES_HJ = false;
+  using I = PDensity::I;
+  __device__ static void load_i(const SweepArgs& a, int p, I& i) { PDensity::load_i(a, p, i); }
+  __device__ static void null_i(I& i) { PDensity::null_i(i); }
+  __device__ static float cut(const I& i, float) { return i.h; }
+  __device__ static float maxcut(float hb, float) { return hb; }
+  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
+    PDensity::stage(a, j, sh, tile, lane);
+  }
+  template <bool COUNT>
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+    float4 p = tile[t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    float q = sqrt_approx(r2) * i.hinv;
+    float aa = fmaxf(1.f - q, 0.f), bb = fmaxf(0.5f - q, 0.f);
+    float a2 = aa * aa, b2 = bb * bb;
+    float w = 2.f * fmaf(-4.f * b2, bb, a2 * aa);
+    float dw = 6.f * fmaf(4.f, b2, -a2);
+    float d2w = 12.f * (aa - 4.f * bb);
+    acc[0] = fmaf(p.w, fmaf(12.f, w, q * fmaf(8.f, dw, q * d2w)), acc[0]);
+    if (COUNT) cnt += r2 < i.h2 ? 1 : 0;
+  }
+  __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
+    float hi = 1.0f / a.h[p];
+    float hi2 = hi * hi;
+    a.o0[p] = SIGMA * hi2 * hi2 * hi * s[0];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// force, Eq. (dvdt) and (dudt), gathered from i's side over r < max(h_i, h_j):
+//   a_i  = -sum_j (m_j C_i w'_i/6 + D_j w'_j/6) (x_i - x_j)/r
+//   du_i = C_i sum_j m_j (w'_i/6) (v_i - v_j).(x_i - x_j)/r
+// with C = 6 sigma A / h^4, D = m C, A = P/(Omega rho^2)
+// ---------------------------------------------------------------------------
+struct PForce {
+  static constexpr int NACC = 4;
+  static constexpr int JW = 3;
+  static constexpr bool USES_HJ = true;
+  struct I {
+    float x, y, z, vx, vy, vz, h, hinv, h2, C;
+    int p;
+  };
+  __device__ static void load_i(const SweepArgs& a, int p, I& i) {
+    float4 q = a.pos4[p];
+    float4 v = a.vel4[p];
+    float4 f = a.fdat[p];
+    i.p = p;
+    i.x = q.x; i.y = q.y; i.z = q.z;
+    i.vx = v.x; i.vy = v.y; i.vz = v.z;
+    i.hinv = v.w;
+    i.h = a.h[p];
+    i.h2 = f.y;
+    i.C = f.z;
+  }
+  __device__ static void null_i(I& i) {
+    i.x = i.y = i.z = i.vx = i.vy = i.vz = 0.f;
+    i.h = i.hinv = i.h2 = i.C = 0.f;
+    i.p = -1;
+  }
+  __device__ static float cut(const I& i, float hj) { return fmaxf(i.h, hj); }
+  __device__ static float maxcut(float hb, float hj) { return fmaxf(hb, hj); }
+  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
+    float4 q = a.pos4[j];
+    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
+    tile[32 + lane] = a.vel4[j];
+    float4 f = a.fdat[j];
+    tile[64 + lane] = make_float4(f.x, f.y, f.z, __int_as_float(j));
+  }
+  template <bool COUNT>
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+    float4 p = tile[t];
+    float4 v = tile[32 + t];
+    float4 f = tile[64 + t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
+    float r = r2 * rinv;
+    float qi = r * i.hinv, qj = r * v.w;
+    float ai = fmaxf(1.f - qi, 0.f), bi = fmaxf(0.5f - qi, 0.f);
+    float aj = fmaxf(1.f - qj, 0.f), bj = fmaxf(0.5f - qj, 0.f);
+    float di = fmaf(4.f * bi, bi, -ai * ai);
+    float dj = fmaf(4.f * bj, bj, -aj * aj);
+    float tm = p.w * di;
+    float coef = fmaf(tm, i.C, f.x * dj) * rinv;
+    acc[0] = fmaf(coef, dx, acc[0]);
+    acc[1] = fmaf(coef, dy, acc[1]);
+    acc[2] = fmaf(coef, dz, acc[2]);
+    float vd = fmaf(i.vz - v.z, dz, fmaf(i.vy - v.y, dy, (i.vx - v.x) * dx));
+    acc[3] = fmaf(tm * rinv, vd, acc[3]);
+    if (COUNT) cnt += (r2 < fmaxf(i.h2, f.y) && __float_as_int(f.w) != i.p) ? 1 : 0;
+  }
+  __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
+    float C = a.fdat[p].z;
+    a.o4[p] = make_float4(-s[0], -s[1], -s[2], C * s[3]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// force adjoint: reverse mode of Eq. (dvdt)/(dudt) gathered from i's side.
+// With xh = (x_i - x_j)/r, G = dW/dr = 6 sigma/h^4 d6, G' = 12 sigma/h^5 e,
+// dG/dh = -sigma/h^5 (24 d6 + 12 q e)  (d6 = w'/6, e = w''/12), and
+// upstream abar (acc) and ubar (du/dt):
+//   gA_i += G_i [ -m_j abar_i.xh + m_i abar_j.xh + ubar_i m_j t ]
+//   gh_i += dG/dh_i [ same bracket ]              (times A_i at the end)
+//   gm_i += Phi abar_j.xh + ubar_j A_j G_j t
+//   gx_i += (c1 - c2 beta - c3 t) xh + c2 b + c3 v_ij
+// where t = v_ij.xh, Phi = A_i G_i + A_j G_j, b = m_i abar_j - m_j abar_i,
+// beta = b.xh, c1 = Phi' beta + (E G'_i + F G'_j) t, c2 = Phi/r,
+// c3 = (E G_i + F G_j)/r, E = ubar_i A_i m_j, F = ubar_j A_j m_i.
+// ---------------------------------------------------------------------------
+struct PForceAdj {
+  static constexpr int NACC = 6;  // gx, gy, gz, gm, gA, gh
+  static constexpr int JW = 4;
+  static constexpr bool USES_HJ = true;
+  struct I {
+    float x, y, z, m, vx, vy, vz, h, hinv, A, ax, ay, az, ub;
+  };
+  __device__ static void load_i(const SweepArgs& a, int p, I& i) {
+    float4 q = a.pos4[p], v = a.vel4[p], g = a.adj4[p];
+    i.x = q.x; i.y = q.y; i.z = q.z; i.m = q.w;
+    i.vx = v.x; i.vy = v.y; i.vz = v.z; i.hinv = v.w;
+    i.h = a.h[p];
+    i.A = a.fdat[p].w;
+    i.ax = g.x; i.ay = g.y; i.az = g.z; i.ub = g.w;
+  }
+  __device__ static void null_i(I& i) {
+    i.x = i.y = i.z = i.m = i.vx = i.vy = i.vz = i.h = i.hinv = i.A = 0.f;
+    i.ax = i.ay = i.az = i.ub = 0.f;
+  }
+  __device__ static float cut(const I& i, float hj) { return fmaxf(i.h, hj); }
+  __device__ static float maxcut(float hb, float hj) { return fmaxf(hb, hj); }
+  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
+    float4 q = a.pos4[j];
+    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
+    tile[32 + lane] = a.vel4[j];
+    tile[64 + lane] = a.adj4[j];
+    tile[96 + lane] = make_float4(a.fdat[j].w, 0.f, 0.f, 0.f);
+  }
+  template <bool COUNT>
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+    float4 p = tile[t], v = tile[32 + t], g = tile[64 + t];
+    float Aj = tile[96 + t].x;
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
+    float r = r2 * rinv;
+    float xx = dx * rinv, xy = dy * rinv, xz = dz * rinv;
+    float qi = r * i.hinv, qj = r * v.w;
+    float ai = fmaxf(1.f - qi, 0.f), bi = fmaxf(0.5f - qi, 0.f);
+    float aj = fmaxf(1.f - qj, 0.f), bj = fmaxf(0.5f - qj, 0.f);
+    float d6i = fmaf(4.f * bi, bi, -ai * ai), d6j = fmaf(4.f * bj, bj, -aj * aj);
+    float ei = fmaf(-4.f, bi, ai), ej = fmaf(-4.f, bj, aj);
+    float hi2 = i.hinv * i.hinv, hj2 = v.w * v.w;
+    float hi4 = hi2 * hi2, hj4 = hj2 * hj2;
+    float Gi = 6.f * SIGMA * hi4 * d6i, Gj = 6.f * SIGMA * hj4 * d6j;
+    float Gpi = 12.f * SIGMA * hi4 * i.hinv * ei, Gpj = 12.f * SIGMA * hj4 * v.w * ej;
+    float Ghi = -SIGMA * hi4 * i.hinv * fmaf(24.f, d6i, 12.f * qi * ei);
+    float vx = i.vx - v.x, vy = i.vy - v.y, vz = i.vz - v.z;
+    float tt = fmaf(vz, xz, fmaf(vy, xy, vx * xx));
+    float sai = fmaf(i.az, xz, fmaf(i.ay, xy, i.ax * xx));
+    float saj = fmaf(g.z, xz, fmaf(g.y, xy, g.x * xx));
+    float br = fmaf(i.ub * p.w, tt, fmaf(i.m, saj, -p.w * sai));
+    acc[4] = fmaf(Gi, br, acc[4]);
+    acc[5] = fmaf(Ghi, br, acc[5]);
+    float Phi = fmaf(i.A, Gi, Aj * Gj);
+    float dPhi = fmaf(i.A, Gpi, Aj * Gpj);
+    float E = i.ub * i.A * p.w, F = g.w * Aj * i.m;
+    acc[3] = fmaf(Phi, saj, fmaf(g.w * Aj * Gj, tt, acc[3]));
+    float bx = fmaf(i.m, g.x, -p.w * i.ax), by = fmaf(i.m, g.y, -p.w * i.ay),
+          bz = fmaf(i.m, g.z, -p.w * i.az);
+    float beta = fmaf(i.m, saj, -p.w * sai);
+    float c1 = fmaf(dPhi, beta, fmaf(E, Gpi, F * Gpj) * tt);
+    float c2 = Phi * rinv;
+    float c3 = fmaf(E, Gi, F * Gj) * rinv;
+    float cx = c1 - c2 * beta - c3 * tt;
+    acc[0] = fmaf(cx, xx, fmaf(c2, bx, fmaf(c3, vx, acc[0])));
+    acc[1] = fmaf(cx, xy, fmaf(c2, by, fmaf(c3, vy, acc[1])));
+    acc[2] = fmaf(cx, xz, fmaf(c2, bz, fmaf(c3, vz, acc[2])));
+    if (COUNT) cnt += (r2 > 0.f && (qi < 1.f || qj < 1.f)) ? 1 : 0;
+  }
+  __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
+    a.o4[p] = make_float4(s[0], s[1], s[2], s[3]);
+    a.o0[p] = s[4];
+    a.o1[p] = s[5];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// density adjoint: reverse mode of Eq. (rho), of d rho/dh and of the
+// implicit h of Eq. (nneigh), gathered from i's side over r < max(h_i, h_j).
+// Per particle k (precomputed): P_k = 2 sigma/h^3 rbar_k,
+// Q_k = 6 sigma/h^4 rbar'_k, R_k = 6 sigma/h^4 rbar_k, S_k = sigma/h^5 rbar'_k,
+// L_k = 64 lambda_k / h_k  (rbar = dL/drho, rbar' = dL/d(drho/dh),
+// lambda_k = hbar_k / (dN_k/dh_k)).  With wh = w/2, d6 = w'/6, e = w''/12:
+//   gm_i += P_j wh_j - Q_j (wh_j + q_j d6_j)          (r < h_j, self included)
+//   T_k   = m_other [R_k d6_k - S_k (24 d6_k + 12 q_k e_k)] - L_k d6_k
+//   gx_i += (T_i + T_j) (x_i - x_j)/r
+// ---------------------------------------------------------------------------
+struct PDensityAdj {
+  static constexpr int NACC = 4;  // gx, gy, gz, gm
+  static constexpr int JW = 3;
+  static constexpr bool USES_HJ = true;
+  struct I {
+    float x, y, z, m, h, hinv, R, S, L;
+  };
+  __device__ static void load_i(const SweepArgs& a, int p, I& i) {
+    float4 q = a.pos4[p], u = a.adj4[p], w = a.adj4b[p];
+    i.x = q.x; i.y = q.y; i.z = q.z; i.m = q.w;
+    i.h = a.h[p];
+    i.hinv = u.x;
+    i.R = u.w; i.S = w.x; i.L = w.y;
+  }
+  __device__ static void null_i(I& i) {
+    i.x = i.y = i.z = i.m = i.h = i.hinv = i.R = i.S = i.L = 0.f;
+  }
+  __device__ static float cut(const I& i, float hj) { return fmaxf(i.h, hj); }
+  __device__ static float maxcut(float hb, float hj) { return fmaxf(hb, hj); }
+  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
+    float4 q = a.pos4[j];
+    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
+    tile[32 + lane] = a.adj4[j];
+    tile[64 + lane] = a.adj4b[j];
+  }
+  template <bool COUNT>
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+    float4 p = tile[t], u = tile[32 + t], w = tile[64 + t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
+    float r = r2 * rinv;
+    float qi = r * i.hinv, qj = r * u.x;
+    float ai = fmaxf(1.f - qi, 0.f), bi = fmaxf(0.5f - qi, 0.f);
+    float aj = fmaxf(1.f - qj, 0.f), bj = fmaxf(0.5f - qj, 0.f);
+    float ai2 = ai * ai, bi2 = bi * bi, aj2 = aj * aj, bj2 = bj * bj;
+    float d6i = fmaf(4.f, bi2, -ai2), d6j = fmaf(4.f, bj2, -aj2);
+    float ei = fmaf(-4.f, bi, ai), ej = fmaf(-4.f, bj, aj);
+    float whj = fmaf(-4.f * bj2, bj, aj2 * aj);
+    acc[3] = fmaf(u.y, whj, fmaf(-u.z, fmaf(qj, d6j, whj), acc[3]));
+    float Ti = fmaf(p.w, fmaf(i.R, d6i, -i.S * fmaf(24.f, d6i, 12.f * qi * ei)), -i.L * d6i);
+    float Tj = fmaf(i.m, fmaf(u.w, d6j, -w.x * fmaf(24.f, d6j, 12.f * qj * ej)), -w.y * d6j);
+    float c = (Ti + Tj) * rinv;
+    acc[0] = fmaf(c, dx, acc[0]);
+    acc[1] = fmaf(c, dy, acc[1]);
+    acc[2] = fmaf(c, dz, acc[2]);
+    if (COUNT) cnt += (r2 > 0.f && (qi < 1.f || qj < 1.f)) ? 1 : 0;
+  }
+  __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
+    float4 o = a.o4[p];
+    a.o4[p] = make_float4(o.x + s[0], o.y + s[1], o.z + s[2], o.w + s[3]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// pair dump (test hook): records accepted pairs in caller indices
+// ---------------------------------------------------------------------------
+template <int FORCE>
+struct PDump {
+  static constexpr int NACC = 1;
+  static constexpr int JW = 2;
+  static constexpr bool USES_HJ = FORCE != 0;
+  struct I {
+    float x, y, z, h, h2;
+    int p;
+    const SweepArgs* a;
+  };
+  __device__ static void load_i(const SweepArgs& a, int p, I& i) {
+    float4 q = a.pos4[p];
+    float h = a.h[p];
+    i.x = q.x; i.y = q.y; i.z = q.z;
+    i.h = h;
+    i.h2 = __fmul_rn(h, h);
+    i.p = p;
+    i.a = &a;
+  }
+  __device__ static void null_i(I& i) {
+    i.x = i.y = i.z = 0.f;
+    i.h = 0.f; i.h2 = -1.f;
+    i.p = -1;
+    i.a = nullptr;
+  }
+  __device__ static float cut(const I& i, float hj) { return FORCE ? fmaxf(i.h, hj) : i.h; }
+  __device__ static float maxcut(float hb, float hj) { return FORCE ? fmaxf(hb, hj) : hb; }
+  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
+    float4 q = a.pos4[j];
+    float h = a.h[j];
+    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
+    tile[32 + lane] = make_float4(__fmul_rn(h, h), __int_as_float(j), 0.f, 0.f);
+  }
+  template <bool COUNT>
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+    if (i.p < 0) return;
+    float4 p = tile[t];
+    float4 e = tile[32 + t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    int j = __float_as_int(e.y);
+    bool ok = FORCE ? (r2 < fmaxf(i.h2, e.x) && j != i.p) : (r2 < i.h2);
+    if (ok) {
+      const SweepArgs& a = *i.a;
+      unsigned long long k = atomicAdd(a.dump_n, 1ull);
+      if ((long long)k < a.dump_cap) {
+        a.dump_i[k] = a.perm[i.p];
+        a.dump_j[k] = a.perm[j];
+      }
+    }
+    (void)acc;
+    (void)cnt;
+  }
+  __device__ static void finalize(const SweepArgs&, int, const float*) {}
+};
+
+// ---------------------------------------------------------------------------
+// the generic persistent sweep
+// ---------------------------------------------------------------------------
+template <class P, bool COUNT>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+  extern __shared__ float4 smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int KS = a.kahan ? 2 : 1;
+  const int accf = a.bmax * P::NACC * KS;
+  const int per_warp = 32 * P::JW + (accf + a.bmax + 3) / 4;
+  float4* tile = smem + warp * per_warp;
+  float* acc = reinterpret_cast<float*>(tile + 32 * P::JW);
+  int* cacc = reinterpret_cast<int*>(acc + accf);
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(a.queue, 1);
+    q = __shfl_sync(FULL, q, 0);
+    if (q >= a.nblock) break;
+    const int b = a.order[q];
+    if (a.blk_active && a.blk_active[b] == 0) continue;
+    const int bf = a.b_first[b], bn = a.b_count[b];
+    for (int k = lane; k < bn * P::NACC * KS; k += 32) acc[k] = 0.f;
+    if (COUNT)
+      for (int k = lane; k < bn; k += 32) cacc[k] = 0;
+    float hb = 0.f;
+    for (int k = lane; k < bn; k += 32) hb = fmaxf(hb, a.h[bf + k]);
+    hb = warp_max(hb);
+    __syncwarp();
+    const long long e1 = a.b_dtoff[b + 1];
+    for (long long e = a.b_dtoff[b]; e < e1; ++e) {
+      const int cj = a.dt_cj[e];
+      const int code = a.dt_code[e];
+      const float4 sh = a.dt_shift[e];
+      const int dir = code & 255, sgn = (code >> 8) - 1;
+      float ux, uy, uz;
+      dir_unit(dir, ux, uy, uz);
+      const float ksh = sort_key(sh.x, sh.y, sh.z, ux, uy, uz);
+      const int ncj = a.n_count[cj];
+      const long long jb = a.n_sbase[cj] + (long long)dir * ncj;
+      const long long ib = 13ll * bf + (long long)dir * bn;
+      const float hj = P::USES_HJ ? a.n_hmax[cj] : 0.f;
+      const float maxcut = P::maxcut(hb, hj) + a.delta;
+      float knear = 0.f;  // s * key of the j nearest to the interface
+      if (sgn > 0) knear = a.s_key[jb] + ksh;
+      else if (sgn < 0) knear = -(a.s_key[jb + ncj - 1] + ksh);
+      for (int c0 = 0; c0 < bn; c0 += 32) {
+        const int t = c0 + lane;
+        const bool vi = t < bn;
+        const int ii = sgn > 0 ? bn - 1 - t : t;
+        int pi = 0;
+        float ki = 0.f;
+        typename P::I I;
+        if (vi) {
+          pi = a.s_idx[ib + ii];
+          ki = a.s_key[ib + ii];
+          P::load_i(a, pi, I);
+        } else {
+          P::null_i(I);
+        }
+        const float cut = P::cut(I, hj);
+        float accr[P::NACC];
+#pragma unroll
+        for (int k = 0; k < P::NACC; ++k) accr[k] = 0.f;
+        int cnt = 0;
+        int jstart = 0;
+        float U;
+        if (sgn != 0) {
+          const float ski = sgn > 0 ? ki : -ki;
+          U = warp_max(vi ? ski + cut + a.delta : -FLT_MAX);
+          const float near_i = __shfl_sync(FULL, ski, 0);
+          if (knear > near_i + maxcut) break;
+          if (knear > U) continue;
+        } else {
+          const float lo = warp_min(vi ? ki - cut - a.delta : FLT_MAX);
+          U = warp_max(vi ? ki + cut + a.delta : -FLT_MAX);
+          jstart = warp_lower_bound(a.s_key + jb, ncj, lo);
+        }
+        for (int j0 = jstart; j0 < ncj; j0 += 32) {
+          const int jj = j0 + lane;
+          const bool vj = jj < ncj;
+          const long long jp = jb + (sgn >= 0 ? jj : ncj - 1 - jj);
+          float sk = FLT_MAX;
+          if (vj) {
+            float kj = a.s_key[jp] + ksh;
+            sk = sgn >= 0 ? kj : -kj;
+          }
+          const bool in = vj && sk <= U;
+          const int nv = __popc(__ballot_sync(FULL, in));
+          if (in) P::stage(a, a.s_idx[jp], sh, tile, lane);
+          __syncwarp();
+          for (int t2 = 0; t2 < nv; ++t2) P::template interact<COUNT>(I, tile, t2, accr, cnt);
+          __syncwarp();
+          if (nv < 32) break;
+        }
+        if (vi) {
+          float* s = acc + (pi - bf) * P::NACC * KS;
+          if (KS == 2) {
+#pragma unroll
+            for (int k = 0; k < P::NACC; ++k) {
+              float S = s[2 * k], Cc = s[2 * k + 1], x = accr[k];
+              float T = S + x;
+              Cc += fabsf(S) >= fabsf(x) ? (S - T) + x : (x - T) + S;
+              s[2 * k] = T;
+              s[2 * k + 1] = Cc;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < P::NACC; ++k) s[k] += accr[k];
+          }
+          if (COUNT) cacc[pi - bf] += cnt;
+        }
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+    int btot = 0;
+    for (int k = lane; k < bn; k += 32) {
+      float v[P::NACC];
+      const float* s = acc + k * P::NACC * KS;
+#pragma unroll
+      for (int m = 0; m < P::NACC; ++m) v[m] = KS == 2 ? s[2 * m] + s[2 * m + 1] : s[m];
+      P::finalize(a, bf + k, v);
+      if (COUNT) {
+        if (a.ocnt) a.ocnt[bf + k] = cacc[k];
+        btot += cacc[k];
+      }
+    }
+    if (COUNT && a.units) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) btot += __shfl_xor_sync(FULL, btot, o);
+      if (lane == 0) atomicAdd(a.units, (unsigned long long)btot);
+    }
+    __syncwarp();
+  }
+}
+
+template <class P, bool COUNT>
+int launch(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
+  const int warps = c->prm.warps_per_cta;
+  const int KS = a.kahan ? 2 : 1;
+  const int accf = a.bmax * P::NACC * KS;
+  const int per_warp = 32 * P::JW + (accf + a.bmax + 3) / 4;
+  size_t smem = (size_t)warps * per_warp * sizeof(float4);
+  auto kern = k_sweep<P, COUNT>;
+  if (smem > 48 * 1024) SPH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, nsm = 0, per_sm = c->prm.ctas_per_sm;
+  SPH_CUDA(cudaGetDevice(&dev));
+  SPH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm <= 0) {
+    SPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem));
+    if (per_sm <= 0) per_sm = 1;
+  }
+  int grid = nsm * per_sm;
+  int maxgrid = div_up(a.nblock, warps);
+  if (grid > maxgrid) grid = maxgrid > 0 ? maxgrid : 1;
+  c->sweep_grid = grid;
+  c->sweep_threads = 32 * warps;
+  SPH_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profile) {
+    if (c->ev_pending.size() >= 4096) SPH_TRY(prof_resolve(c));
+    a.units = c->prof_units.as<unsigned long long>() + c->ev_pending.size();
+    SPH_CUDA(cudaMemsetAsync(a.units, 0, sizeof(unsigned long long), s));
+    e0 = ev_get(c);
+    e1 = ev_get(c);
+    SPH_CUDA(cudaEventRecord(e0, s));
+  }
+  { kern<<<grid, 32 * warps, smem, s>>>(a); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  if (c->profile) {
+    SPH_CUDA(cudaEventRecord(e1, s));
+    c->ev_pending.push_back({c->cur_phase, e0, e1});
+  }
+  return SPH_OK;
+}
+
+}  // namespace
+
+cudaEvent_t ev_get(sph_ctx* c) {
+  if (c->ev_pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = c->ev_pool.back();
+  c->ev_pool.pop_back();
+  return e;
+}
+
+int prof_resolve(sph_ctx* c) {
+  std::vector<unsigned long long> units(c->ev_pending.size());
+  if (!units.empty())
+    SPH_CUDA(cudaMemcpy(units.data(), c->prof_units.p, units.size() * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost));
+  size_t k = 0;
+  for (auto& e : c->ev_pending) {
+    SPH_CUDA(cudaEventSynchronize(e.b));
+    float ms = 0.f;
+    SPH_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
+    if (e.phase >= 0 && e.phase < 8) {
+      c->prof_ms[e.phase] += ms;
+      c->prof_n[e.phase] += 1;
+      c->prof_units_acc[e.phase] += units[k];
+    }
+    ++k;
+    c->ev_pool.push_back(e.a);
+    c->ev_pool.push_back(e.b);
+  }
+  c->ev_pending.clear();
+  return SPH_OK;
+}
+
+int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t s) {
+  if (c->nblock == 0) return SPH_OK;
+  c->cur_phase = phase;
+  if (c->profile && phase < PH_DUMP_DENSITY) counting = 1;
+  SweepArgs a{};
+  a.nblock = c->nblock;
+  a.order = c->b_order.as<int>();
+  a.b_first = c->b_first.as<int>();
+  a.b_count = c->b_count.as<int>();
+  a.b_dtoff = c->b_dtoff.as<long long>();
+  a.dt_cj = c->dt_cj.as<int>();
+  a.dt_code = c->dt_code.as<int>();
+  a.dt_shift = c->dt_shift.as<float4>();
+  a.n_count = c->n_count.as<int>();
+  a.n_sbase = c->n_sbase.as<long long>();
+  a.n_hmax = c->n_hmax.as<float>();
+  a.s_key = c->s_key.as<float>();
+  a.s_idx = c->s_idx.as<int>();
+  a.pos4 = c->pos4.as<float4>();
+  a.h = c->h.as<float>();
+  a.vel4 = c->vel4.as<float4>();
+  a.fdat = c->fdat.as<float4>();
+  a.blk_active = only_active ? c->blk_active.as<int>() : nullptr;
+  a.queue = c->queue.as<int>();
+  a.status = c->status.as<int>();
+  double emax = 0;
+  for (int b = 0; b < c->nbox; ++b) emax = std::max(emax, c->box_L[b] / (double)(1 << c->box_t[b]));
+  a.delta = (float)(emax * (1.0 / 65536.0));
+  a.kahan = c->prm.kahan ? 1 : 0;
+  a.bmax = c->prm.block_max;
+  a.ocnt = counting ? c->cnt_i.as<int>() : nullptr;
+  switch (phase) {
+    case PH_DENSITY:
+      a.o0 = c->rho.as<float>();
+      a.o1 = c->drho.as<float>();
+      a.o2 = c->nngb.as<float>();
+      a.o3 = c->dnngb.as<float>();
+      return counting ? launch<PDensity, true>(c, a, s) : launch<PDensity, false>(c, a, s);
+    case PH_DENSITY_D2:
+      a.o0 = c->d2rho.as<float>();
+      return counting ? launch<PDensityD2, true>(c, a, s) : launch<PDensityD2, false>(c, a, s);
+    case PH_FORCE:
+      a.o4 = c->acc4.as<float4>();
+      return counting ? launch<PForce, true>(c, a, s) : launch<PForce, false>(c, a, s);
+    case PH_FORCE_ADJ:
+      a.adj4 = c->adj4.as<float4>();
+      a.o4 = c->g_x4.as<float4>();
+      a.o0 = c->g_A.as<float>();
+      a.o1 = c->g_h_s.as<float>();
+      return counting ? launch<PForceAdj, true>(c, a, s) : launch<PForceAdj, false>(c, a, s);
+    case PH_DENSITY_ADJ:
+      a.adj4 = c->adj4.as<float4>();
+      a.adj4b = c->adj4b.as<float4>();
+      a.o4 = c->g_x4.as<float4>();
+      return counting ? launch<PDensityAdj, true>(c, a, s) : launch<PDensityAdj, false>(c, a, s);
+    case PH_DUMP_DENSITY:
+    case PH_DUMP_FORCE:
+      a.perm = c->perm.as<int>();
+      a.dump_i = c->dump_pi;
+      a.dump_j = c->dump_pj;
+      a.dump_n = c->counters.as<unsigned long long>();
+      a.dump_cap = c->dump_cap;
+      a.kahan = 0;
+      return phase == PH_DUMP_DENSITY ? launch<PDump<0>, false>(c, a, s)
+                                      : launch<PDump<1>, false>(c, a, s);
+    default:
+      return SPH_ERR_INVALID_ARG;
+  }
+}

@@ -1,0 +1,179 @@
+"""Context object over the C ABI.  Tensors must be CUDA tensors; outputs
+are allocated with torch and filled by the library on the current stream."""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import SphParams, SphStats, check
+
+
+def default_params(**overrides) -> SphParams:
+    lib = _lib.load()
+    p = SphParams()
+    lib.sph_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _f32(t, shape=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("SPH tensors must live on the GPU")
+    t = t.detach().to(torch.float32).contiguous()
+    if shape is not None:
+        t = t.reshape(shape)
+    return t
+
+
+class SPH:
+    """One decomposition + state.  Typical use::
+
+        s = SPH()
+        s.build(pos)                 # (N, 3) float64, unit periodic box
+        out = s.density(m)           # h, rho, omega
+        acc, dudt = s.force(u, vel)
+    """
+
+    def __init__(self, **params):
+        self.lib = _lib.load()
+        self.params = default_params(**params)
+        h = C.c_void_p()
+        check(self.lib.sph_create(C.byref(self.params), C.byref(h)), "sph_create")
+        self.h = h
+        self.n = 0
+
+    def close(self):
+        if self.h:
+            self.lib.sph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- build ---------------------------------------------------------------
+    def build(self, pos, box=1.0, h_guess=None):
+        pos = pos.detach().to(torch.float64).contiguous()
+        hg = _f32(h_guess)
+        self._keep = (pos, hg)
+        self.n = pos.shape[0]
+        check(self.lib.sph_build(self.h, self.n, _ptr(pos), float(box), _ptr(hg), _stream()),
+              "sph_build")
+
+    def build_batch(self, pos, offsets, boxes, h_guess=None):
+        pos = pos.detach().to(torch.float64).contiguous()
+        hg = _f32(h_guess)
+        nbox = len(boxes)
+        off = (C.c_int64 * (nbox + 1))(*[int(v) for v in offsets])
+        bx = (C.c_double * nbox)(*[float(v) for v in boxes])
+        self._keep = (pos, hg)
+        self.n = pos.shape[0]
+        check(self.lib.sph_build_batch(self.h, nbox, off, bx, _ptr(pos), _ptr(hg), _stream()),
+              "sph_build_batch")
+
+    # -- density -------------------------------------------------------------
+    def density_fixed_h(self, m, h, count=False):
+        m, h = _f32(m), _f32(h)
+        z = lambda: torch.empty(self.n, device=m.device, dtype=torch.float32)
+        rho, drho, nngb, dnngb = z(), z(), z(), z()
+        cnt = torch.empty(self.n, device=m.device, dtype=torch.int32) if count else None
+        check(self.lib.sph_density_fixed_h(self.h, _ptr(m), _ptr(h), _ptr(rho), _ptr(drho),
+                                           _ptr(nngb), _ptr(dnngb), _ptr(cnt), _stream()),
+              "sph_density_fixed_h")
+        return dict(rho=rho, drho_dh=drho, nngb=nngb, dnngb_dh=dnngb, count=cnt)
+
+    def density(self, m):
+        m = _f32(m)
+        z = lambda: torch.empty(self.n, device=m.device, dtype=torch.float32)
+        h, rho, omega = z(), z(), z()
+        it = C.c_int32(0)
+        check(self.lib.sph_density(self.h, _ptr(m), _ptr(h), _ptr(rho), _ptr(omega),
+                                   C.byref(it), _stream()), "sph_density")
+        return dict(h=h, rho=rho, omega=omega, iters=int(it.value))
+
+    # -- force ---------------------------------------------------------------
+    def force(self, u, vel=None, count=False):
+        u = _f32(u)
+        vel = _f32(vel, (self.n, 3)) if vel is not None else None
+        acc = torch.empty((self.n, 3), device=u.device, dtype=torch.float32)
+        dudt = torch.empty(self.n, device=u.device, dtype=torch.float32)
+        cnt = torch.empty(self.n, device=u.device, dtype=torch.int32) if count else None
+        check(self.lib.sph_force(self.h, _ptr(u), _ptr(vel), _ptr(acc), _ptr(dudt), _ptr(cnt),
+                                 _stream()), "sph_force")
+        return acc, dudt, cnt
+
+    # -- adjoints ------------------------------------------------------------
+    def force_adjoint(self, g_acc, g_dudt=None):
+        g_acc = _f32(g_acc, (self.n, 3))
+        g_dudt = _f32(g_dudt)
+        dev = g_acc.device
+        g_pos = torch.empty((self.n, 3), device=dev, dtype=torch.float32)
+        z = lambda: torch.empty(self.n, device=dev, dtype=torch.float32)
+        g_m, g_u, g_rho, g_drho, g_h = z(), z(), z(), z(), z()
+        check(self.lib.sph_force_adjoint(self.h, _ptr(g_acc), _ptr(g_dudt), _ptr(g_pos), _ptr(g_m),
+                                         _ptr(g_u), _ptr(g_rho), _ptr(g_drho), _ptr(g_h), _stream()),
+              "sph_force_adjoint")
+        return dict(g_pos=g_pos, g_m=g_m, g_u=g_u, g_rho=g_rho, g_drho=g_drho, g_h=g_h)
+
+    def density_adjoint(self, g_rho, g_drho, g_h, g_pos, g_m):
+        check(self.lib.sph_density_adjoint(self.h, _ptr(_f32(g_rho)), _ptr(_f32(g_drho)),
+                                           _ptr(_f32(g_h)), _ptr(g_pos), _ptr(g_m), _stream()),
+              "sph_density_adjoint")
+        return g_pos, g_m
+
+    def adjoint(self, g_rho=None, g_acc=None, g_dudt=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        g_pos = torch.empty((self.n, 3), device=dev, dtype=torch.float32)
+        g_m = torch.empty(self.n, device=dev, dtype=torch.float32)
+        g_u = torch.empty(self.n, device=dev, dtype=torch.float32)
+        check(self.lib.sph_adjoint(self.h, _ptr(_f32(g_rho)), _ptr(_f32(g_acc, (self.n, 3)) if g_acc is not None else None),
+                                   _ptr(_f32(g_dudt)), _ptr(g_pos), _ptr(g_m), _ptr(g_u), _stream()),
+              "sph_adjoint")
+        return g_pos, g_m, g_u
+
+    # -- introspection ---------------------------------------------------------
+    def pairs(self, phase, cap=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cap = cap or max(1024, self.n * 128)
+        pi = torch.empty(cap, device=dev, dtype=torch.int32)
+        pj = torch.empty(cap, device=dev, dtype=torch.int32)
+        n = C.c_int64(0)
+        check(self.lib.sph_pairs_dump(self.h, int(phase), cap, _ptr(pi), _ptr(pj), C.byref(n),
+                                      _stream()), "sph_pairs_dump")
+        return pi[: n.value], pj[: n.value]
+
+    def stats(self) -> dict:
+        st = SphStats()
+        check(self.lib.sph_get_stats(self.h, C.byref(st)), "sph_get_stats")
+        d = {k: getattr(st, k) for k, _ in SphStats._fields_}
+        d["top_level"] = list(st.top_level)[: max(1, min(8, st.nbox))]
+        d["sweep_ms"] = list(st.sweep_ms)
+        d["sweep_launches"] = list(st.sweep_launches)
+        d["sweep_units"] = list(st.sweep_units)
+        return d
+
+    def profile(self, enable=True):
+        check(self.lib.sph_profile(self.h, 1 if enable else 0), "sph_profile")
+
+    def launch_count(self) -> int:
+        return int(self.lib.sph_launch_count())
+
+    def sync_status(self):
+        check(self.lib.sph_sync_status(self.h, _stream()), "sph_sync_status")
