@@ -123,7 +123,7 @@ __global__ void k_rebuild_guess(long long n, const float* h, const float* hlim, 
                                 float* hg) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  hg[s] = (flag[s] & HF_LIMIT) ? 1.5f * hlim[s] : h[s];
+  hg[s] = (flag[s] & HF_LIMIT) ? 2.0f * hlim[s] : h[s];
 }
 
 // ---- ghost step (text after Eq. (dudt)) and force-side per-particle data
@@ -396,13 +396,16 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
     int host[2] = {1, 0};
     int it = 0;
     SPH_CUDA(cudaMemsetAsync(c->blk_active.p, 0, 4 * (size_t)c->nblock, s));
+    // nlim accumulates over the whole solve: a particle flagged at its cell
+    // limit in any iteration leaves the active set and must trigger the rebuild
+    SPH_CUDA(cudaMemsetAsync(nlim, 0, sizeof(int), s));
     for (; it < c->prm.max_newton; ++it) {
       { k_block_active<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, s>>>(
           c->nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->h_flag.as<int>(),
           c->blk_active.as<int>()); note_launch(); }
       SPH_CUDA(cudaGetLastError());
       SPH_TRY(run_sweep(c, PH_DENSITY, 1, 0, s));
-      SPH_CUDA(cudaMemsetAsync(nact, 0, 2 * sizeof(int), s));
+      SPH_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), s));
       { k_hsolve_update<<<div_up(n, TPB), TPB, 0, s>>>(
           n, c->h.as<float>(), c->hlim.as<float>(), c->nngb.as<float>(), c->dnngb.as<float>(),
           c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_flag.as<int>(), c->prm.n_ngb,

@@ -145,11 +145,16 @@ def test_momentum_conservation_gpu():
 
 def test_errors_are_reported():
     from paper_1404_2303_gb300._lib import SphError
-    d = C.random_box(200, 3, "uniform")  # h ~ 0.4 > box/4
+    d = C.random_box(200, 3, "uniform")  # solved h ~ 0.4 > box/4: no valid top grid
     s = _sph()
-    with pytest.raises(SphError) as e:
-        s.build(_t(d["x"]))
+    with pytest.raises(SphError) as e:  # an explicit guess above box/4 is rejected
+        s.build(_t(d["x"]), h_guess=_t(np.full(200, 0.4, np.float32)))
     assert e.value.code == -1
+    s.build(_t(d["x"]))  # the estimate is clamped below box/4 ...
+    with pytest.raises(SphError) as e:  # ... and the solve reports the cell limit
+        s.density(_t(d["m"]))
+    assert e.value.code == -5
     s2 = _sph()
-    with pytest.raises(SphError):
-        s2.density(_t(d["m"]))  # not built
+    with pytest.raises(SphError) as e:
+        s2.density(_t(d["m"]))  # nothing built
+    assert e.value.code == -6
