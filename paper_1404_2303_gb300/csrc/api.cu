@@ -280,7 +280,7 @@ void sph_destroy(sph_ctx* c) {
                  &c->perm, &c->perm_alt, &c->xs, &c->pos4, &c->h, &c->hguess, &c->hlim, &c->pnode,
                  &c->n_first, &c->n_count, &c->n_parent, &c->n_child0, &c->n_top, &c->n_flags,
                  &c->n_need, &c->n_ijk, &c->n_box, &c->n_hmax, &c->n_hbuild, &c->n_hlim,
-                 &c->n_sbase, &c->t_cur, &c->t_next, &c->t_final_pair, &c->t_final_self, &c->t_cnt,
+                 &c->n_sbase, &c->n_nblk, &c->n_blk0, &c->b_hmax, &c->t_cur, &c->t_next, &c->t_final_pair, &c->t_final_self, &c->t_cnt,
                  &c->t_cnt2, &c->t_off, &c->t_off2, &c->b_first, &c->b_count, &c->b_leaf,
                  &c->b_dtoff, &c->b_order, &c->b_cost, &c->dt_cj, &c->dt_code, &c->dt_shift,
                  &c->adj_off, &c->adj_list, &c->s_key, &c->s_idx, &c->rho, &c->drho, &c->nngb,
@@ -432,7 +432,14 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
     { k_rebuild_guess<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), c->hlim.as<float>(),
                                                    c->h_flag.as<int>(), c->hguess.as<float>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
-    SPH_TRY(build_from_guess(c, s));
+    {
+      int r = build_from_guess(c, s);
+      if (r != SPH_OK) {
+        c->built = false;  // the decomposition is half rebuilt
+        // no top grid can hold the h this particle set needs (h > box/4)
+        return r == SPH_ERR_INVALID_ARG ? SPH_ERR_CELL_LIMIT : r;
+      }
+    }
     SPH_TRY(ensure_state(c));
     SPH_TRY(prep_mass(c, m, s));
   }

@@ -54,11 +54,6 @@ __device__ __forceinline__ float warp_max(float v) {
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
-__device__ __forceinline__ int warp_sum(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // ---------------------------------------------------------------- keys
 __global__ void k_keys(const double* pos, long long n, const long long* off, const double* Ls,
@@ -122,36 +117,6 @@ __global__ void k_init_top(int ntop, const int* top_base, const int* box_t, int 
   na.ijk[id] = make_int4(ix, iy, iz, t);
 }
 
-// warp per node: max build h and the split decision of Section 3.2 / 4.2
-__global__ void k_node_stats(int g0, int g1, int mode, int split_count, float split_frac, int K,
-                             const float* hs, const double* Ls, NodeArrays na, int* split) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  int node = g0 + warp;
-  if (node >= g1) return;
-  int f = na.first[node], c = na.count[node];
-  int4 ijk = na.ijk[node];
-  double e = Ls[na.box[node]] / (double)(1ll << ijk.w);
-  float half = (float)(0.5 * e);
-  float hm = 0.f;
-  int small = 0;
-  for (int k = lane; k < c; k += 32) {
-    float hv = hs[f + k];
-    hm = fmaxf(hm, hv);
-    small += hv < half ? 1 : 0;
-  }
-  hm = warp_max(hm);
-  small = warp_sum(small);
-  if (lane == 0) {
-    na.hbuild[node] = hm;
-    int s;
-    if (mode == 0)
-      s = (c > split_count) && ((float)small > split_frac * (float)c) && (ijk.w < K);
-    else
-      s = (c > EST_SPLIT) && (ijk.w < K);
-    split[node - g0] = s;
-  }
-}
 
 __global__ void k_make_children(int g0, int g1, int next, const int* split, const int* soff,
                                 const unsigned long long* keys, int K, NodeArrays na) {
@@ -182,14 +147,6 @@ __global__ void k_make_children(int g0, int g1, int next, const int* split, cons
   }
 }
 
-__global__ void k_leaf_particles(int ncell, const int* first, const int* count, const int* child0,
-                                 int* pnode) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= ncell || child0[warp] >= 0) return;
-  int f = first[warp], c = count[warp];
-  for (int k = lane; k < c; k += 32) pnode[f + k] = warp;
-}
 
 // h estimate from the count-only octree: local number density of the
 // leaf's parent (or of the leaf itself at the top level), turned into the
@@ -498,7 +455,6 @@ __global__ void k_sort_base(int ncell, const int* need, const int* child0, const
   else sbase[id] = -1;
 }
 
-constexpr int MERGE_MAXSUB = 256;
 
 __device__ __forceinline__ int count_less(const float* k, const int* ix, int n, float kv, int iv) {
   int lo = 0, hi = n;
@@ -509,69 +465,6 @@ __device__ __forceinline__ int count_less(const float* k, const int* ix, int n, 
   return lo;
 }
 
-// CTA per node: merge the sub-lists (children, or the leaf's blocks) of
-// every needed direction by ranking each element in the other sub-lists
-__global__ void k_merge(int g0, int g1, const int* need, const int* child0, const int* count,
-                        const int* nblk, const int* blk0, const int* b_first, const int* b_count,
-                        const long long* sbase, float* s_key, int* s_idx, int* status) {
-  __shared__ long long sb[MERGE_MAXSUB];
-  __shared__ int sc[MERGE_MAXSUB];
-  __shared__ int spre[MERGE_MAXSUB + 1];
-  __shared__ int nsub;
-  int node = g0 + blockIdx.x;
-  if (node >= g1) return;
-  int nd = need[node];
-  bool leaf = child0[node] < 0;
-  if (nd == 0 || count[node] == 0 || (leaf && nblk[node] <= 1)) return;
-  int cnt = count[node];
-  long long ob = sbase[node];
-  for (int d = 0; d < SPH_NDIR; ++d) {
-    if (!((nd >> d) & 1)) continue;
-    if (threadIdx.x == 0) {
-      int ns = 0;
-      if (leaf) {
-        int nb = nblk[node];
-        if (nb > MERGE_MAXSUB) { atomicOr(status, ST_CAPACITY); nb = 0; }
-        for (int k = 0; k < nb; ++k) {
-          int bi = blk0[node] + k;
-          sb[ns] = 13ll * b_first[bi] + (long long)d * b_count[bi];
-          sc[ns] = b_count[bi];
-          ++ns;
-        }
-      } else {
-        for (int k = 0; k < 8; ++k) {
-          int ch = child0[node] + k;
-          int cc = count[ch];
-          if (cc == 0) continue;
-          sb[ns] = sbase[ch] + (long long)d * cc;
-          sc[ns] = cc;
-          ++ns;
-        }
-      }
-      spre[0] = 0;
-      for (int k = 0; k < ns; ++k) spre[k + 1] = spre[k] + sc[k];
-      nsub = ns;
-    }
-    __syncthreads();
-    int ns = nsub;
-    for (int e = threadIdx.x; e < spre[ns]; e += blockDim.x) {
-      int s = 0;
-      while (spre[s + 1] <= e) ++s;
-      int l = e - spre[s];
-      float kv = s_key[sb[s] + l];
-      int iv = s_idx[sb[s] + l];
-      int rank = l;
-      for (int o = 0; o < ns; ++o) {
-        if (o == s) continue;
-        rank += count_less(s_key + sb[o], s_idx + sb[o], sc[o], kv, iv);
-      }
-      long long dst = ob + (long long)d * cnt + rank;
-      s_key[dst] = kv;
-      s_idx[dst] = iv;
-    }
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------- interaction lists
 __global__ void k_pair_degree(int np, const int4* pairs, int* deg) {
@@ -664,17 +557,222 @@ __global__ void k_order_from_keys(int n, const unsigned long long* keys, int* or
   if (i < n) order[i] = (int)(keys[i] & 0xffffffffu);
 }
 
-// warp per node: max of the current h over the node's particles
-__global__ void k_node_hmax(int ncell, const int* first, const int* count, const float* h,
-                            float* hmax) {
+
+// ---------------------------------------------------------------- flat tree kernels
+// Every particle carries the node that holds it at the current generation
+// (pcur, -1 once its node is a leaf), so per-generation statistics are one
+// pass over the particles with warp-aggregated atomics, whatever the node
+// sizes (a single top cell may hold 10^5 particles of a clump).
+__global__ void k_pcur_init(long long n, const unsigned long long* keys, const int* box_t,
+                            const int* top_base, int K, int* pcur) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  unsigned long long key = keys[s];
+  int b = (int)(key >> (3 * K));
+  int t = box_t[b];
+  unsigned long long tm = (key >> (3 * (K - t))) & ((1ull << (3 * t)) - 1);
+  int ix = compact3(tm >> 2), iy = compact3(tm >> 1), iz = compact3(tm);
+  int nb = 1 << t;
+  pcur[s] = top_base[b] + (ix * nb + iy) * nb + iz;
+}
+
+__global__ void k_stats_flat(long long n, const int* pcur, const float* hs, const int4* ijk,
+                             const int* box, const double* Ls, int use_h, int* acc_hmax,
+                             int* acc_small) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int node = s < n ? pcur[s] : -1;
+  int hb = 0, small = 0;
+  if (node >= 0 && use_h) {
+    float hv = hs[s];
+    double e = Ls[box[node]] / (double)(1ll << ijk[node].w);
+    hb = __float_as_int(hv);
+    small = hv < (float)(0.5 * e) ? 1 : 0;
+  }
+  unsigned peers = __match_any_sync(0xffffffffu, node);
+  int leader = __ffs(peers) - 1;
+  // reduce within the peer group
+  int mh = hb, ms = small;
+  unsigned rest = peers;
+  int sum = 0, mx = 0;
+  while (rest) {
+    int l = __ffs(rest) - 1;
+    rest &= rest - 1;
+    int a = __shfl_sync(peers, mh, l);
+    int b = __shfl_sync(peers, ms, l);
+    mx = max(mx, a);
+    sum += b;
+  }
+  if (lane == leader && node >= 0) {
+    if (use_h) atomicMax(&acc_hmax[node], mx);
+    atomicAdd(&acc_small[node], sum);
+  }
+}
+
+__global__ void k_split_decide(int g0, int g1, int mode, int split_count, float split_frac, int K,
+                               const int* count, const int4* ijk, const int* acc_hmax,
+                               const int* acc_small, float* hbuild, int* split) {
+  int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g1) return;
+  int c = count[node];
+  hbuild[node] = __int_as_float(acc_hmax[node]);
+  int sp;
+  if (mode == 0)
+    sp = (c > split_count) && ((float)acc_small[node] > split_frac * (float)c) && (ijk[node].w < K);
+  else
+    sp = (c > EST_SPLIT) && (ijk[node].w < K);
+  split[node - g0] = sp;
+}
+
+__global__ void k_pcur_update(long long n, int* pcur, const unsigned long long* keys,
+                              const int* child0, const int4* ijk, int K, int* pnode) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int node = pcur[s];
+  if (node < 0) return;
+  int c0 = child0[node];
+  if (c0 < 0) {
+    pnode[s] = node;
+    pcur[s] = -1;
+    return;
+  }
+  int lvl = ijk[node].w + 1;
+  int k = (int)((keys[s] >> (3 * (K - lvl))) & 7ull);
+  pcur[s] = c0 + k;
+}
+
+__global__ void k_box_hmax(long long n, const long long* off, int nbox, const float* h, int* out) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int b = s < n ? box_of(off, nbox, s) : -1;
+  int v = s < n ? __float_as_int(h[s]) : 0;
+  unsigned peers = __match_any_sync(0xffffffffu, b);
+  unsigned rest = peers;
+  int mx = 0;
+  while (rest) {
+    int l = __ffs(rest) - 1;
+    rest &= rest - 1;
+    mx = max(mx, __shfl_sync(peers, v, l));
+  }
+  if (lane == __ffs(peers) - 1 && b >= 0) atomicMax(&out[b], mx);
+}
+
+// ---------------------------------------------------------------- flat merge
+// Elements of every (node, needed direction) of one generation form one flat
+// index space; each thread ranks one element of one sub-list (child cell or
+// leaf block) against the node's other sub-lists by binary search.
+__device__ __forceinline__ bool mergeable(int node, const int* need, const int* child0,
+                                          const int* nblk, const int* count) {
+  return need[node] != 0 && count[node] > 0 && !(child0[node] < 0 && nblk[node] <= 1);
+}
+
+__global__ void k_merge_count(int g0, int g1, const int* need, const int* child0, const int* nblk,
+                              const int* count, long long* elems) {
+  int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g1) return;
+  elems[node - g0] = mergeable(node, need, child0, nblk, count)
+                         ? (long long)count[node] * __popc(need[node])
+                         : 0;
+}
+
+__global__ void k_merge_flat(int g0, int ng, const long long* off, long long total, const int* need,
+                             const int* child0, const int* count, const int* nblk, const int* blk0,
+                             const int* b_first, const int* b_count, const long long* sbase,
+                             float* s_key, int* s_idx) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    // node: last index with off[i] <= e
+    int lo = 0, hi = ng;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (off[mid] <= e) lo = mid; else hi = mid;
+    }
+    int node = g0 + lo;
+    long long loc = e - off[lo];
+    int cnt = count[node];
+    int slot = (int)(loc / cnt);
+    int l = (int)(loc - (long long)slot * cnt);
+    int nd = need[node];
+    int d = 0;
+    for (int k = 0; k <= slot; ++k) {
+      d = __ffs(nd) - 1;
+      nd &= nd - 1;
+    }
+    const bool leaf = child0[node] < 0;
+    const int nsub = leaf ? nblk[node] : 8;
+    // locate the element's sub-list
+    int s = 0, base = 0;
+    long long sb = 0;
+    int sc = 0;
+    for (s = 0; s < nsub; ++s) {
+      if (leaf) {
+        int bi = blk0[node] + s;
+        sc = b_count[bi];
+        sb = 13ll * b_first[bi] + (long long)d * sc;
+      } else {
+        int ch = child0[node] + s;
+        sc = count[ch];
+        sb = sc > 0 ? sbase[ch] + (long long)d * sc : 0;
+      }
+      if (l < base + sc) break;
+      base += sc;
+    }
+    int li = l - base;
+    float kv = s_key[sb + li];
+    int iv = s_idx[sb + li];
+    int rank = li;
+    for (int o = 0; o < nsub; ++o) {
+      if (o == s) continue;
+      long long ob;
+      int oc;
+      if (leaf) {
+        int bi = blk0[node] + o;
+        oc = b_count[bi];
+        ob = 13ll * b_first[bi] + (long long)d * oc;
+      } else {
+        int ch = child0[node] + o;
+        oc = count[ch];
+        if (oc == 0) continue;
+        ob = sbase[ch] + (long long)d * oc;
+      }
+      rank += count_less(s_key + ob, s_idx + ob, oc, kv, iv);
+    }
+    long long dst = sbase[node] + (long long)d * cnt + rank;
+    s_key[dst] = kv;
+    s_idx[dst] = iv;
+  }
+}
+
+// ---------------------------------------------------------------- node h maxima
+__global__ void k_block_hmax(int nblock, const int* b_first, const int* b_count, const float* h,
+                             float* out) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (warp >= ncell) return;
-  int f = first[warp], c = count[warp];
+  if (warp >= nblock) return;
+  int f = b_first[warp], c = b_count[warp];
   float m = 0.f;
   for (int k = lane; k < c; k += 32) m = fmaxf(m, h[f + k]);
   m = warp_max(m);
-  if (lane == 0) hmax[warp] = m;
+  if (lane == 0) out[warp] = m;
+}
+
+__global__ void k_leaf_hmax(int ncell, const int* child0, const int* nblk, const int* blk0,
+                            const float* bh, float* hmax) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ncell || child0[id] >= 0) return;
+  float m = 0.f;
+  for (int k = 0; k < nblk[id]; ++k) m = fmaxf(m, bh[blk0[id] + k]);
+  hmax[id] = m;
+}
+
+__global__ void k_internal_hmax(int g0, int g1, const int* child0, float* hmax) {
+  int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g1) return;
+  int c0 = child0[node];
+  if (c0 < 0) return;
+  float m = 0.f;
+  for (int k = 0; k < 8; ++k) m = fmaxf(m, hmax[c0 + k]);
+  hmax[node] = m;
 }
 
 }  // namespace
@@ -752,26 +850,46 @@ static int build_tree(sph_ctx* c, int mode, cudaStream_t s) {
   int g0 = 0, g1 = c->ntop;
   int maxd = 0;
   for (int b = 0; b < c->nbox; ++b) maxd = std::max(maxd, c->box_t[b]);
+  SPH_TRY(dbuf_ensure(c->pnode, sizeof(int) * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->tmp_c, sizeof(int) * (size_t)n));  // pcur
+  int* pcur = c->tmp_c.as<int>();
+  { k_pcur_init<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), c->d_box_t.as<int>(),
+                                              c->d_top_base.as<int>(), K, pcur); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
   for (;;) {
     int ng = g1 - g0;
     SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (ng + 1)));
     SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (ng + 1)));
+    SPH_TRY(grow_copy(c->n_flags, sizeof(int) * (size_t)g0, sizeof(int) * (size_t)g1 + 64, s));
+    SPH_TRY(grow_copy(c->n_need, sizeof(int) * (size_t)g0, sizeof(int) * (size_t)g1 + 64, s));
+    int* acc_h = c->n_flags.as<int>();   // scratch during the build: max h bits
+    int* acc_s = c->n_need.as<int>();    // scratch during the build: small-h counts
+    SPH_CUDA(cudaMemsetAsync(acc_h + g0, 0, sizeof(int) * ng, s));
+    SPH_CUDA(cudaMemsetAsync(acc_s + g0, 0, sizeof(int) * ng, s));
     na = nbufs.arrays();
-    { k_node_stats<<<div_up((long long)ng * 32, TPB), TPB, 0, s>>>(
-        g0, g1, mode, c->prm.split_count, c->prm.split_frac, K, c->hguess.as<float>(),
-        c->d_box_L.as<double>(), na, c->t_cnt.as<int>()); note_launch(); }
+    { k_stats_flat<<<div_up(n, TPB), TPB, 0, s>>>(n, pcur, c->hguess.as<float>(), na.ijk, na.box,
+                                                 c->d_box_L.as<double>(), mode == 0, acc_h, acc_s); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    { k_split_decide<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, mode, c->prm.split_count,
+                                                    c->prm.split_frac, K, na.count, na.ijk, acc_h,
+                                                    acc_s, na.hbuild, c->t_cnt.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
     SPH_TRY(scan_exclusive_i32(c->t_cnt.as<int>(), c->t_off.as<int>(), ng,
                                c->t_off.as<int>() + ng, c->scan_tmp, s));
     int nsplit = 0;
     SPH_TRY(d2h(&nsplit, c->t_off.as<int>() + ng, s));
-    if (nsplit == 0) break;
-    SPH_TRY(nbufs.grow((size_t)g1, (size_t)g1 + 8 * (size_t)nsplit, s));
-    na = nbufs.arrays();
-    { k_make_children<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, g1, c->t_cnt.as<int>(),
-                                                    c->t_off.as<int>(),
-                                                    c->keys.as<unsigned long long>(), K, na); note_launch(); }
+    if (nsplit > 0) {
+      SPH_TRY(nbufs.grow((size_t)g1, (size_t)g1 + 8 * (size_t)nsplit, s));
+      na = nbufs.arrays();
+      { k_make_children<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, g1, c->t_cnt.as<int>(),
+                                                       c->t_off.as<int>(),
+                                                       c->keys.as<unsigned long long>(), K, na); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+    }
+    { k_pcur_update<<<div_up(n, TPB), TPB, 0, s>>>(n, pcur, c->keys.as<unsigned long long>(),
+                                                  na.child0, na.ijk, K, c->pnode.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
+    if (nsplit == 0) break;
     g0 = g1;
     g1 += 8 * nsplit;
     c->gen_start.push_back(g1);
@@ -779,11 +897,6 @@ static int build_tree(sph_ctx* c, int mode, cudaStream_t s) {
   }
   c->ncell = g1;
   c->max_depth = maxd;
-  SPH_TRY(dbuf_ensure(c->pnode, sizeof(int) * (size_t)n));
-  { k_leaf_particles<<<div_up((long long)c->ncell * 32, TPB), TPB, 0, s>>>(
-      c->ncell, c->n_first.as<int>(), c->n_count.as<int>(), c->n_child0.as<int>(),
-      c->pnode.as<int>()); note_launch(); }
-  SPH_CUDA(cudaGetLastError());
   return SPH_OK;
 }
 
@@ -791,27 +904,13 @@ static int choose_top_levels(sph_ctx* c, cudaStream_t s) {
   // per-box max of the build h (host reduction over a D2H copy of per-box maxima)
   const int n = (int)c->n;
   std::vector<float> hmax(c->nbox, 0.f);
-  {
-    // small kernel-free approach: copy h to host in chunks is too slow for large n;
-    // reuse k_node_hmax over pseudo-nodes = boxes
-    SPH_TRY(dbuf_ensure(c->tmp_a, sizeof(int) * c->nbox * 2 + 64));
-    SPH_TRY(dbuf_ensure(c->tmp_b, sizeof(float) * c->nbox + 64));
-    std::vector<int> fc(2 * c->nbox);
-    for (int b = 0; b < c->nbox; ++b) {
-      fc[b] = (int)c->box_off[b];
-      fc[c->nbox + b] = (int)(c->box_off[b + 1] - c->box_off[b]);
-    }
-    SPH_CUDA(cudaMemcpyAsync(c->tmp_a.p, fc.data(), sizeof(int) * 2 * c->nbox,
-                             cudaMemcpyHostToDevice, s));
-    { k_node_hmax<<<div_up((long long)c->nbox * 32, TPB), TPB, 0, s>>>(
-        c->nbox, c->tmp_a.as<int>(), c->tmp_a.as<int>() + c->nbox, c->hguess.as<float>(),
-        c->tmp_b.as<float>()); note_launch(); }
-    SPH_CUDA(cudaGetLastError());
-    SPH_CUDA(cudaMemcpyAsync(hmax.data(), c->tmp_b.p, sizeof(float) * c->nbox,
-                             cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaStreamSynchronize(s));
-  }
-  (void)n;
+  SPH_TRY(dbuf_ensure(c->tmp_b, sizeof(int) * c->nbox + 64));
+  SPH_CUDA(cudaMemsetAsync(c->tmp_b.p, 0, sizeof(int) * c->nbox, s));
+  { k_box_hmax<<<div_up(n, TPB), TPB, 0, s>>>(n, c->d_box_off.as<long long>(), c->nbox,
+                                             c->hguess.as<float>(), c->tmp_b.as<int>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_CUDA(cudaMemcpyAsync(hmax.data(), c->tmp_b.p, sizeof(float) * c->nbox, cudaMemcpyDeviceToHost, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
   c->box_t.assign(c->nbox, 2);
   for (int b = 0; b < c->nbox; ++b) {
     double L = c->box_L[b];
@@ -830,10 +929,22 @@ static int choose_top_levels(sph_ctx* c, cudaStream_t s) {
 
 int compute_node_hmax(sph_ctx* c, cudaStream_t s) {
   SPH_TRY(dbuf_ensure(c->n_hmax, sizeof(float) * (size_t)c->ncell));
-  { k_node_hmax<<<div_up((long long)c->ncell * 32, TPB), TPB, 0, s>>>(
-      c->ncell, c->n_first.as<int>(), c->n_count.as<int>(), c->h.as<float>(),
-      c->n_hmax.as<float>()); note_launch(); }
+  SPH_TRY(dbuf_ensure(c->b_hmax, sizeof(float) * (size_t)(c->nblock + 1)));
+  { k_block_hmax<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, s>>>(
+      c->nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->h.as<float>(),
+      c->b_hmax.as<float>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
+  { k_leaf_hmax<<<div_up(c->ncell, TPB), TPB, 0, s>>>(c->ncell, c->n_child0.as<int>(),
+                                                     c->n_nblk.as<int>(), c->n_blk0.as<int>(),
+                                                     c->b_hmax.as<float>(), c->n_hmax.as<float>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  for (int g = (int)c->gen_start.size() - 2; g >= 0; --g) {
+    int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
+    if (g1 <= g0) continue;
+    { k_internal_hmax<<<div_up(g1 - g0, TPB), TPB, 0, s>>>(g0, g1, c->n_child0.as<int>(),
+                                                          c->n_hmax.as<float>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
   return SPH_OK;
 }
 
@@ -934,8 +1045,9 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
   // blocks
   SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (ncell + 1)));
   SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (ncell + 1)));
-  SPH_TRY(dbuf_ensure(c->tmp_c, sizeof(int) * (ncell + 1)));  // nblk per node (kept)
-  int* nblk = c->tmp_c.as<int>();
+  SPH_TRY(dbuf_ensure(c->n_nblk, sizeof(int) * (ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->n_blk0, sizeof(int) * (ncell + 1)));
+  int* nblk = c->n_nblk.as<int>();
   { k_leaf_nblk<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, c->n_child0.as<int>(),
                                                  c->n_count.as<int>(), c->prm.block_max, nblk); note_launch(); }
   SPH_CUDA(cudaGetLastError());
@@ -948,13 +1060,12 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
   SPH_TRY(dbuf_ensure(c->b_count, sizeof(int) * (nblock + 1)));
   SPH_TRY(dbuf_ensure(c->b_leaf, sizeof(int) * (nblock + 1)));
   SPH_TRY(dbuf_ensure(c->n_need, sizeof(int) * (ncell + 1)));  // reused below as need
-  SPH_TRY(dbuf_ensure(c->adj_off, sizeof(int) * (ncell + 1)));  // temporarily blk0
-  DBuf blk0_buf;
-  SPH_TRY(dbuf_ensure(blk0_buf, sizeof(int) * (ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->adj_off, sizeof(int) * (ncell + 1)));
+  int* blk0 = c->n_blk0.as<int>();
   { k_make_blocks<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, c->n_first.as<int>(),
                                                    c->n_count.as<int>(), nblk, c->t_off.as<int>(),
                                                    c->b_first.as<int>(), c->b_count.as<int>(),
-                                                   c->b_leaf.as<int>(), blk0_buf.as<int>()); note_launch(); }
+                                                   c->b_leaf.as<int>(), blk0); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   // block sorts: lists of all 13 directions at [13 first, 13 (first + count))
   // needs
@@ -997,16 +1108,26 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
   }
   for (int g = (int)c->gen_start.size() - 2; g >= 0; --g) {
     int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
-    if (g1 <= g0) continue;
-    { k_merge<<<g1 - g0, 256, 0, s>>>(g0, g1, need, c->n_child0.as<int>(), c->n_count.as<int>(),
-                                    nblk, blk0_buf.as<int>(), c->b_first.as<int>(),
-                                    c->b_count.as<int>(), c->n_sbase.as<long long>(),
-                                    c->s_key.as<float>(), c->s_idx.as<int>(),
-                                    c->status.as<int>()); note_launch(); }
+    int ng = g1 - g0;
+    if (ng <= 0) continue;
+    SPH_TRY(dbuf_ensure(sz, sizeof(long long) * (size_t)(2 * ng + 2)));
+    long long* el = sz.as<long long>();
+    long long* eo = el + (ng + 1);
+    { k_merge_count<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, need, c->n_child0.as<int>(), nblk,
+                                                   c->n_count.as<int>(), el); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    SPH_TRY(scan_exclusive_i64(el, eo, ng, eo + ng, c->scan_tmp, s));
+    long long total = 0;
+    SPH_TRY(d2h(&total, eo + ng, s));
+    if (total == 0) continue;
+    int grid = (int)std::min<long long>(div_up(total, TPB), 152ll * 64);
+    { k_merge_flat<<<grid, TPB, 0, s>>>(g0, ng, eo, total, need, c->n_child0.as<int>(),
+                                       c->n_count.as<int>(), nblk, blk0, c->b_first.as<int>(),
+                                       c->b_count.as<int>(), c->n_sbase.as<long long>(),
+                                       c->s_key.as<float>(), c->s_idx.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
   }
   dbuf_free(sz);
-  dbuf_free(blk0_buf);
 
   // ---- interaction lists per block
   int* deg = c->t_cnt.as<int>();

@@ -105,6 +105,7 @@ struct sph_ctx {
   DBuf n_hbuild;  // float max h at build time
   DBuf n_hlim;    // float
   DBuf n_sbase;   // long long: base of the node's 13 sorted lists (-1 none)
+  DBuf n_nblk, n_blk0;  // leaves: number of particle blocks and the first block
 
   // tasks
   int nself = 0, npair = 0;
@@ -116,7 +117,7 @@ struct sph_ctx {
   // blocks
   int nblock = 0, nleaf = 0;
   int64_t ndt = 0;
-  DBuf b_first, b_count, b_leaf, b_dtoff, b_order, b_cost;
+  DBuf b_first, b_count, b_leaf, b_dtoff, b_order, b_cost, b_hmax;
   DBuf dt_cj;      // int
   DBuf dt_code;    // int: dir | (sgn+1) << 8
   DBuf dt_shift;   // float4 (sx, sy, sz, 0)
