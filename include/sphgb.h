@@ -225,6 +225,43 @@ int sph_profile(sph_ctx* ctx, int32_t enable);
 /* Copy the statistics of the last calls into *out. */
 int sph_get_stats(sph_ctx* ctx, sph_stats* out);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this exists
+ * for callers that cannot call cudaMalloc, e.g. code that runs inside a
+ * framework owning all device memory (a custom-call or plugin interface
+ * that only hands in preplanned buffers), code on a real-time path where an
+ * allocation may block or fail, or applications that must not grow their
+ * device footprint after start-up.
+ *
+ * Density with the smoothing-length solve of Eq. (nneigh) for ONE small
+ * periodic box [0, box)^3, by direct summation over all particle pairs (no
+ * cell decomposition, no context), allocating nothing.  The per-particle
+ * solver scratch (FP64 bracket, flags, sums) lives in a file-scope device
+ * array sized for SPH_NOALLOC_MAX_N particles (about 0.6 MB) that every
+ * GPU loading this library holds until the process exits.
+ *   n        particles, 1..SPH_NOALLOC_MAX_N (larger n: SPH_ERR_INVALID_ARG
+ *            and a message on stderr)
+ *   pos      n x 3 float64 positions (device)
+ *   m        n float32 masses (device)
+ *   h_guess  n float32 initial h (device, nullable: the h holding n_ngb
+ *            particles at the mean density)
+ *   n_ngb    target weighted neighbour number (48 in the paper)
+ *   max_iter Newton/bisection iterations at most
+ *   h_out, rho_out  n float32 outputs (device; either may be NULL)
+ *   iters    out (HOST, nullable): iterations used
+ * Returns SPH_ERR_CELL_LIMIT if some h would exceed box/2 and
+ * SPH_ERR_H_NOT_CONVERGED after max_iter.  Synchronises `stream`.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array,
+ * which keeps the last call's contents: calls that overlap on the GPU
+ * (different streams or host threads) race and must be serialised by the
+ * caller. */
+#define SPH_NOALLOC_MAX_N 16384
+int sph_density_small_noalloc(int32_t n, const double* pos, double box, const float* m,
+                              const float* h_guess, float n_ngb, int32_t max_iter, float* h_out,
+                              float* rho_out, int32_t* iters, void* stream);
+
 /* Number of kernel launches this library has issued since it was loaded
  * (all contexts). */
 int64_t sph_launch_count(void);

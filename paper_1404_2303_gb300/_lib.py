@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsphgb.so")
 
 SPH_OK = 0
+NOALLOC_MAX_N = 16384  # SPH_NOALLOC_MAX_N of include/sphgb.h
 STATUS_NAMES = {
     0: "SPH_OK", -1: "SPH_ERR_INVALID_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_OOM",
     -4: "SPH_ERR_H_NOT_CONVERGED", -5: "SPH_ERR_CELL_LIMIT", -6: "SPH_ERR_NOT_BUILT",
@@ -62,6 +63,8 @@ SIGNATURES = {
     "sph_get_stats": (C.c_int, [P, C.POINTER(SphStats)]),
     "sph_profile": (C.c_int, [P, C.c_int32]),
     "sph_launch_count": (C.c_int64, []),
+    "sph_density_small_noalloc": (C.c_int, [C.c_int32, P, C.c_double, P, P, C.c_float, C.c_int32,
+                                            P, P, C.POINTER(C.c_int32), P]),
     "sph_sync_status": (C.c_int, [P, P]),
     "sph_status_string": (C.c_char_p, [C.c_int]),
 }

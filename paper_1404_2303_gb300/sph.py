@@ -40,6 +40,25 @@ def _f32(t, shape=None):
     return t
 
 
+def density_small_noalloc(pos, m, h_guess=None, box=1.0, n_ngb=48.0, max_iter=64):
+    """Density + smoothing-length solve for one small box through the
+    allocation-free entry point (direct summation, n <= 16384): the library
+    allocates nothing; the output tensors below are allocated here by torch,
+    on the caller's side of the interface.  Returns (h, rho, iterations)."""
+    lib = _lib.load()
+    pos = pos.detach().to(torch.float64).contiguous()
+    m = _f32(m)
+    hg = _f32(h_guess)
+    n = pos.shape[0]
+    h = torch.empty(n, device=pos.device, dtype=torch.float32)
+    rho = torch.empty(n, device=pos.device, dtype=torch.float32)
+    it = C.c_int32(0)
+    check(lib.sph_density_small_noalloc(n, _ptr(pos), float(box), _ptr(m), _ptr(hg), float(n_ngb),
+                                        int(max_iter), _ptr(h), _ptr(rho), C.byref(it), _stream()),
+          "sph_density_small_noalloc")
+    return h, rho, int(it.value)
+
+
 class SPH:
     """One decomposition + state.  Typical use::
 
