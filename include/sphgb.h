@@ -79,6 +79,9 @@ typedef struct sph_params {
   float h_tol;          /* converged when |N - n_ngb| <= h_tol * n_ngb; 2^-19 */
   int32_t warps_per_cta;/* sweep kernels: warps per CTA (1..8); 4 */
   int32_t ctas_per_sm;  /* sweep kernels: resident CTAs per SM used to size the persistent grid; 0 = occupancy */
+  int32_t h_est_mode;   /* h estimate when no guess is given: 0 density of the leaf's parent,
+                           1 the lower of leaf and parent densities; 1 */
+  float h_est_factor;   /* multiplies the estimated h (a margin against rebuilds); 1.5 */
 } sph_params;
 
 /* Statistics of the last build and sweeps (host copy). */
@@ -104,6 +107,7 @@ typedef struct sph_stats {
   int32_t sweep_launches[8];
   int64_t sweep_units[8];    /* pairs accepted by those launches: directed (i<-j) for
                                 phases 0 and 1, ordered i != j pairs for 2..4 */
+  int64_t sweep_candidates[8]; /* (i, j) candidates those launches evaluated */
   int32_t sweep_grid;        /* CTAs of the last sweep launch */
   int32_t sweep_threads;     /* threads per CTA of the sweep launches */
 } sph_stats;

@@ -26,6 +26,7 @@ class SphParams(C.Structure):
         ("split_frac", C.c_float), ("block_max", C.c_int32), ("max_newton", C.c_int32),
         ("max_rebuild", C.c_int32), ("kahan", C.c_int32), ("morton_bits", C.c_int32),
         ("h_tol", C.c_float), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
+        ("h_est_mode", C.c_int32), ("h_est_factor", C.c_float),
     ]
 
 
@@ -36,7 +37,7 @@ class SphStats(C.Structure):
         ("max_depth", C.c_int32), ("top_level", C.c_int32 * 8), ("newton_iters", C.c_int32),
         ("rebuilds", C.c_int32), ("density_interactions", C.c_int64), ("force_pairs", C.c_int64),
         ("sorted_entries", C.c_int64), ("sweep_ms", C.c_double * 8),
-        ("sweep_launches", C.c_int32 * 8), ("sweep_units", C.c_int64 * 8), ("sweep_grid", C.c_int32), ("sweep_threads", C.c_int32),
+        ("sweep_launches", C.c_int32 * 8), ("sweep_units", C.c_int64 * 8), ("sweep_candidates", C.c_int64 * 8), ("sweep_grid", C.c_int32), ("sweep_threads", C.c_int32),
     ]
 
 

@@ -81,8 +81,15 @@ __global__ void k_hsolve_update(long long n, float* h, const float* hlim, const 
     H = hd;
     fl |= HF_HI_VALID;
   }
+  // Newton step on ln N(ln h) = ln n_ngb: the same derivative dN/dh, taken
+  // in log-log form, lands on the root in one step when N grows like h^3
   double dN = (double)dnngb[s];
-  double hn = dN > 0 ? hd - f / dN : -1.0;
+  double Nv = (double)nngb[s];
+  double slope = (dN > 0 && Nv > 0) ? hd * dN / Nv : 0.0;
+  // (FP32 transcendentals: the step is only a proposal inside the FP64 bracket)
+  double hn = slope > 1e-3
+                  ? hd * (double)__expf((__logf(n_ngb) - __logf((float)Nv)) / (float)slope)
+                  : -1.0;
   if (fl & HF_HI_VALID) {
     if (!(hn > L && hn < H)) hn = 0.5 * (L + H);
     if (H - L <= 2.4e-7 * hd) {  // bracket below FP32 resolution
@@ -247,6 +254,8 @@ void sph_default_params(sph_params* p) {
   p->h_tol = 1.0f / 524288.0f;  // 2^-19
   p->warps_per_cta = 4;
   p->ctas_per_sm = 0;
+  p->h_est_mode = 1;
+  p->h_est_factor = 1.5f;
 }
 
 int sph_create(const sph_params* p, sph_ctx** out) {
@@ -257,7 +266,8 @@ int sph_create(const sph_params* p, sph_ctx** out) {
   if (!(q.n_ngb > 32.f / 3.f) || !(q.gamma > 1.f) || q.split_count < 1 || !(q.split_frac > 0.f) ||
       q.block_max < 32 || q.block_max > 256 || q.max_newton < 1 || q.max_rebuild < 0 ||
       q.morton_bits < 8 || q.morton_bits > 20 || !(q.h_tol > 0.f) || q.warps_per_cta < 1 ||
-      q.warps_per_cta > 8 || q.ctas_per_sm < 0)
+      q.warps_per_cta > 8 || q.ctas_per_sm < 0 || q.h_est_mode < 0 || q.h_est_mode > 1 ||
+      !(q.h_est_factor > 0.f))
     return SPH_ERR_INVALID_ARG;
   sph_ctx* c = new sph_ctx();
   c->prm = q;
@@ -523,6 +533,7 @@ int sph_profile(sph_ctx* c, int32_t enable) {
     c->prof_ms[k] = 0;
     c->prof_n[k] = 0;
     c->prof_units_acc[k] = 0;
+    c->prof_cand_acc[k] = 0;
   }
   if (enable) SPH_TRY(dbuf_ensure(c->prof_units, 4096 * sizeof(unsigned long long)));
   c->profile = enable != 0;
@@ -537,6 +548,7 @@ int sph_get_stats(sph_ctx* c, sph_stats* out) {
     st.sweep_ms[k] = c->prof_ms[k];
     st.sweep_launches[k] = c->prof_n[k];
     st.sweep_units[k] = (int64_t)c->prof_units_acc[k];
+    st.sweep_candidates[k] = (int64_t)c->prof_cand_acc[k];
   }
   st.sweep_grid = c->sweep_grid;
   st.sweep_threads = c->sweep_threads;

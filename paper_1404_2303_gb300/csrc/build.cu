@@ -118,27 +118,23 @@ __global__ void k_init_top(int ntop, const int* top_base, const int* box_t, int 
 }
 
 
+// structural fields of the 8 children of each split node; their particle
+// ranges are filled by k_pcur_update from the Morton-key boundaries
 __global__ void k_make_children(int g0, int g1, int next, const int* split, const int* soff,
-                                const unsigned long long* keys, int K, NodeArrays na) {
+                                NodeArrays na) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int node = g0 + i;
   if (node >= g1 || !split[i]) return;
   int c0 = next + 8 * soff[i];
   na.child0[node] = c0;
-  int f = na.first[node], e = f + na.count[node];
   int4 p = na.ijk[node];
   int b = na.box[node];
   int lvl = p.w + 1;
-  int sh = 3 * (K - lvl);
   for (int k = 0; k < 8; ++k) {
     int cx = 2 * p.x + ((k >> 2) & 1), cy = 2 * p.y + ((k >> 1) & 1), cz = 2 * p.z + (k & 1);
-    unsigned long long lo = ((unsigned long long)b << (3 * K)) | (morton3(cx, cy, cz) << sh);
-    unsigned long long hi = lo + (1ull << sh);
-    int cf = lower_bound_u64(keys, f, e, lo);
-    int ce = lower_bound_u64(keys, cf, e, hi);
     int id = c0 + k;
-    na.first[id] = cf;
-    na.count[id] = ce - cf;
+    na.first[id] = 0;
+    na.count[id] = 0;
     na.parent[id] = node;
     na.child0[id] = -1;
     na.top[id] = na.top[node];
@@ -147,13 +143,12 @@ __global__ void k_make_children(int g0, int g1, int next, const int* split, cons
   }
 }
 
-
 // h estimate from the count-only octree: local number density of the
 // leaf's parent (or of the leaf itself at the top level), turned into the
 // h whose sphere holds N_ngb particles at that density
 __global__ void k_h_estimate(long long n, const int* pnode, const int* parent, const int* count,
                              const int4* ijk, const int* box, const double* Ls, float n_ngb,
-                             float* hout) {
+                             int mode, float factor, float* hout) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int node = pnode[s];
@@ -162,7 +157,13 @@ __global__ void k_h_estimate(long long n, const int* pnode, const int* parent, c
   double L = Ls[box[use]];
   double e = L / (double)(1ll << ijk[use].w);
   double dens = (double)count[use] / (e * e * e);
-  double h = cbrt(3.0 * (double)n_ngb / (4.0 * M_PI * dens));
+  if (mode == 1 && par >= 0 && count[node] >= 8) {
+    // the lower of the leaf's and its parent's densities: a leaf at the
+    // edge of a clump does not inherit the clump's density
+    double el = L / (double)(1ll << ijk[node].w);
+    dens = fmin(dens, (double)count[node] / (el * el * el));
+  }
+  double h = (double)factor * cbrt(3.0 * (double)n_ngb / (4.0 * M_PI * dens));
   h = fmin(h, 0.24 * L);
   hout[s] = (float)h;
 }
@@ -347,67 +348,69 @@ __global__ void k_make_blocks(int ncell, const int* first, const int* count, con
 }
 
 // ---------------------------------------------------------------- sorts
-// one CTA per block: bitonic sort of (key, global index) for each of the
-// 13 directions; ties cannot occur because indices are distinct
+// (key, global index) order: ties cannot occur because indices are distinct
 constexpr int SORT_MAX = 256;
 
 __device__ __forceinline__ bool kv_less(float ka, int ia, float kb, int ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
 
-__global__ void __launch_bounds__(SORT_MAX) k_sort_blocks(const int* b_first, const int* b_count,
-                                                          const float4* pos4, float* s_key,
-                                                          int* s_idx) {
-  __shared__ float sk[SORT_MAX];
-  __shared__ int si[SORT_MAX];
-  __shared__ float px[SORT_MAX], py[SORT_MAX], pz[SORT_MAX];
-  int b = blockIdx.x;
-  int f = b_first[b], c = b_count[b];
-  int t = threadIdx.x;
-  if (t < c) {
-    float4 p = pos4[f + t];
-    px[t] = p.x; py[t] = p.y; pz[t] = p.z;
-  }
-  int np2 = 1;
-  while (np2 < c) np2 <<= 1;
-  __syncthreads();
-  for (int d = 0; d < SPH_NDIR; ++d) {
+// one warp per (block, direction): bitonic sort of (key, index) pairs in
+// shared memory, padded to a power of two >= 32
+constexpr int WS_WARPS = 8;
+
+__global__ void __launch_bounds__(WS_WARPS * 32)
+    k_sort_blocks_warp(int nblock, const int* b_first, const int* b_count, const float4* pos4,
+                       float* s_key, int* s_idx) {
+  __shared__ float sk[WS_WARPS][SORT_MAX];
+  __shared__ int si[WS_WARPS][SORT_MAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long items = (long long)nblock * SPH_NDIR;
+  for (long long item = (long long)blockIdx.x * WS_WARPS + warp; item < items;
+       item += (long long)gridDim.x * WS_WARPS) {
+    const int b = (int)(item / SPH_NDIR), d = (int)(item % SPH_NDIR);
+    const int f = b_first[b], c = b_count[b];
     float ux, uy, uz;
     dir_unit(d, ux, uy, uz);
-    if (t < np2) {
+    int np2 = 32;
+    while (np2 < c) np2 <<= 1;
+    float* K = sk[warp];
+    int* X = si[warp];
+    for (int t = lane; t < np2; t += 32) {
       if (t < c) {
-        sk[t] = sort_key(px[t], py[t], pz[t], ux, uy, uz);
-        si[t] = f + t;
+        float4 p = pos4[f + t];
+        K[t] = sort_key(p.x, p.y, p.z, ux, uy, uz);
+        X[t] = f + t;
       } else {
-        sk[t] = __int_as_float(0x7f800000);
-        si[t] = 0x7fffffff;
+        K[t] = __int_as_float(0x7f800000);
+        X[t] = 0x7fffffff;
       }
     }
-    __syncthreads();
+    __syncwarp();
     for (int k = 2; k <= np2; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
-        if (t < np2) {
+        for (int t = lane; t < np2; t += 32) {
           int p = t ^ j;
           if (p > t) {
             bool up = (t & k) == 0;
-            float ka = sk[t], kb = sk[p];
-            int ia = si[t], ib = si[p];
+            float ka = K[t], kb = K[p];
+            int ia = X[t], ib = X[p];
             bool sw = up ? kv_less(kb, ib, ka, ia) : kv_less(ka, ia, kb, ib);
             if (sw) {
-              sk[t] = kb; sk[p] = ka;
-              si[t] = ib; si[p] = ia;
+              K[t] = kb; K[p] = ka;
+              X[t] = ib; X[p] = ia;
             }
           }
         }
-        __syncthreads();
+        __syncwarp();
       }
     }
-    if (t < c) {
-      long long o = 13ll * f + (long long)d * c + t;
-      s_key[o] = sk[t];
-      s_idx[o] = si[t];
+    const long long o = 13ll * f + (long long)d * c;
+    for (int t = lane; t < c; t += 32) {
+      s_key[o + t] = K[t];
+      s_idx[o + t] = X[t];
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -624,8 +627,13 @@ __global__ void k_split_decide(int g0, int g1, int mode, int split_count, float 
   split[node - g0] = sp;
 }
 
+// advance every particle to its child at the next generation (or retire it
+// at its leaf) and record the children's particle ranges: a particle whose
+// predecessor (successor) in Morton order lies in another child starts
+// (ends) its child's range
 __global__ void k_pcur_update(long long n, int* pcur, const unsigned long long* keys,
-                              const int* child0, const int4* ijk, int K, int* pnode) {
+                              const int* child0, const int* first, const int* count,
+                              const int4* ijk, int K, int* pnode, int* cfirst, int* cend) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int node = pcur[s];
@@ -636,9 +644,20 @@ __global__ void k_pcur_update(long long n, int* pcur, const unsigned long long* 
     pcur[s] = -1;
     return;
   }
-  int lvl = ijk[node].w + 1;
-  int k = (int)((keys[s] >> (3 * (K - lvl))) & 7ull);
-  pcur[s] = c0 + k;
+  int sh = 3 * (K - ijk[node].w - 1);
+  int k = (int)((keys[s] >> sh) & 7ull);
+  int child = c0 + k;
+  pcur[s] = child;
+  long long f = first[node], e = f + count[node];
+  if (s == f || (int)((keys[s - 1] >> sh) & 7ull) != k) cfirst[child] = (int)s;
+  if (s == e - 1 || (int)((keys[s + 1] >> sh) & 7ull) != k) cend[child] = (int)(s + 1);
+}
+
+__global__ void k_child_counts(int c0, int c1, const int* cend, int* first, int* count) {
+  int id = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= c1) return;
+  int e = cend[id];
+  count[id] = e > 0 ? e - first[id] : 0;
 }
 
 __global__ void k_box_hmax(long long n, const long long* off, int nbox, const float* h, int* out) {
@@ -878,17 +897,26 @@ static int build_tree(sph_ctx* c, int mode, cudaStream_t s) {
                                c->t_off.as<int>() + ng, c->scan_tmp, s));
     int nsplit = 0;
     SPH_TRY(d2h(&nsplit, c->t_off.as<int>() + ng, s));
+    int* cend = nullptr;
     if (nsplit > 0) {
       SPH_TRY(nbufs.grow((size_t)g1, (size_t)g1 + 8 * (size_t)nsplit, s));
       na = nbufs.arrays();
       { k_make_children<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, g1, c->t_cnt.as<int>(),
-                                                       c->t_off.as<int>(),
-                                                       c->keys.as<unsigned long long>(), K, na); note_launch(); }
+                                                       c->t_off.as<int>(), na); note_launch(); }
       SPH_CUDA(cudaGetLastError());
+      SPH_TRY(grow_copy(c->t_cnt2, 0, sizeof(int) * ((size_t)g1 + 8 * (size_t)nsplit), s));
+      cend = c->t_cnt2.as<int>();
+      SPH_CUDA(cudaMemsetAsync(cend + g1, 0, sizeof(int) * 8 * (size_t)nsplit, s));
     }
     { k_pcur_update<<<div_up(n, TPB), TPB, 0, s>>>(n, pcur, c->keys.as<unsigned long long>(),
-                                                  na.child0, na.ijk, K, c->pnode.as<int>()); note_launch(); }
+                                                  na.child0, na.first, na.count, na.ijk, K,
+                                                  c->pnode.as<int>(), na.first, cend); note_launch(); }
     SPH_CUDA(cudaGetLastError());
+    if (nsplit > 0) {
+      { k_child_counts<<<div_up(8 * nsplit, TPB), TPB, 0, s>>>(g1, g1 + 8 * nsplit, cend, na.first,
+                                                              na.count); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+    }
     if (nsplit == 0) break;
     g0 = g1;
     g1 += 8 * nsplit;
@@ -993,9 +1021,10 @@ static int build_tasks(sph_ctx* c, cudaStream_t s) {
     SPH_TRY(scan_exclusive_i32(nfs, ofs, nt, ofs + nt, c->scan_tmp, s));
     SPH_TRY(scan_exclusive_i32(nfp, ofp, nt, ofp + nt, c->scan_tmp, s));
     int tot[3];
-    SPH_TRY(d2h(&tot[0], och + nt, s));
-    SPH_TRY(d2h(&tot[1], ofs + nt, s));
-    SPH_TRY(d2h(&tot[2], ofp + nt, s));
+    SPH_CUDA(cudaMemcpyAsync(&tot[0], och + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaMemcpyAsync(&tot[1], ofs + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaMemcpyAsync(&tot[2], ofp + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
     SPH_TRY(dbuf_ensure(c->t_next, sizeof(int4) * (size_t)(tot[0] + 1)));
     if ((size_t)(nfs_total + tot[1]) > fs_cap) {
       fs_cap = (size_t)(nfs_total + tot[1]) * 2 + 1024;
@@ -1101,9 +1130,10 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
                                                  13ll * n, c->n_sbase.as<long long>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   if (nblock > 0) {
-    { k_sort_blocks<<<nblock, SORT_MAX, 0, s>>>(c->b_first.as<int>(), c->b_count.as<int>(),
-                                              c->pos4.as<float4>(), c->s_key.as<float>(),
-                                              c->s_idx.as<int>()); note_launch(); }
+    int grid = (int)std::min<long long>(div_up((long long)nblock * SPH_NDIR, WS_WARPS), 152ll * 32);
+    { k_sort_blocks_warp<<<grid, WS_WARPS * 32, 0, s>>>(nblock, c->b_first.as<int>(),
+                                                       c->b_count.as<int>(), c->pos4.as<float4>(),
+                                                       c->s_key.as<float>(), c->s_idx.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
   }
   for (int g = (int)c->gen_start.size() - 2; g >= 0; --g) {
@@ -1223,7 +1253,8 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
     { k_h_estimate<<<div_up(n, TPB), TPB, 0, s>>>(n, c->pnode.as<int>(), c->n_parent.as<int>(),
                                                 c->n_count.as<int>(), c->n_ijk.as<int4>(),
                                                 c->n_box.as<int>(), c->d_box_L.as<double>(),
-                                                c->prm.n_ngb, c->hguess.as<float>()); note_launch(); }
+                                                c->prm.n_ngb, c->prm.h_est_mode, c->prm.h_est_factor,
+                                                c->hguess.as<float>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
   }
   return build_from_guess(c, s);

@@ -161,6 +161,7 @@ struct sph_ctx {
   std::vector<cudaEvent_t> ev_pool;
   DBuf prof_units;  // unsigned long long per pending profiled launch
   unsigned long long prof_units_acc[8] = {0};
+  unsigned long long prof_cand_acc[8] = {0};
   double prof_ms[8] = {0};
   int prof_n[8] = {0};
 };

@@ -549,6 +549,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         for (int k = 0; k < P::NACC; ++k) accr[k] = 0.f;
         int cnt = 0;
         int jstart = 0;
+        int ncand = 0;
         float U;
         if (sgn != 0) {
           const float ski = sgn > 0 ? ki : -ki;
@@ -575,6 +576,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           if (in) P::stage(a, a.s_idx[jp], sh, tile, lane);
           __syncwarp();
           for (int t2 = 0; t2 < nv; ++t2) P::template interact<COUNT>(I, tile, t2, accr, cnt);
+          if (COUNT && vi) ncand += nv;
           __syncwarp();
           if (nv < 32) break;
         }
@@ -594,6 +596,11 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
             for (int k = 0; k < P::NACC; ++k) s[k] += accr[k];
           }
           if (COUNT) cacc[pi - bf] += cnt;
+        }
+        if (COUNT && a.units) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(FULL, ncand, o);
+          if (lane == 0) atomicAdd(a.units + 1, (unsigned long long)ncand);
         }
       }
       __syncwarp();
@@ -644,9 +651,9 @@ int launch(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
   SPH_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), s));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile) {
-    if (c->ev_pending.size() >= 4096) SPH_TRY(prof_resolve(c));
-    a.units = c->prof_units.as<unsigned long long>() + c->ev_pending.size();
-    SPH_CUDA(cudaMemsetAsync(a.units, 0, sizeof(unsigned long long), s));
+    if (c->ev_pending.size() >= 2048) SPH_TRY(prof_resolve(c));
+    a.units = c->prof_units.as<unsigned long long>() + 2 * c->ev_pending.size();
+    SPH_CUDA(cudaMemsetAsync(a.units, 0, 2 * sizeof(unsigned long long), s));
     e0 = ev_get(c);
     e1 = ev_get(c);
     SPH_CUDA(cudaEventRecord(e0, s));
@@ -674,7 +681,7 @@ cudaEvent_t ev_get(sph_ctx* c) {
 }
 
 int prof_resolve(sph_ctx* c) {
-  std::vector<unsigned long long> units(c->ev_pending.size());
+  std::vector<unsigned long long> units(2 * c->ev_pending.size());
   if (!units.empty())
     SPH_CUDA(cudaMemcpy(units.data(), c->prof_units.p, units.size() * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost));
@@ -686,7 +693,8 @@ int prof_resolve(sph_ctx* c) {
     if (e.phase >= 0 && e.phase < 8) {
       c->prof_ms[e.phase] += ms;
       c->prof_n[e.phase] += 1;
-      c->prof_units_acc[e.phase] += units[k];
+      c->prof_units_acc[e.phase] += units[2 * k];
+      c->prof_cand_acc[e.phase] += units[2 * k + 1];
     }
     ++k;
     c->ev_pool.push_back(e.a);

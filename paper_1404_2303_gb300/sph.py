@@ -186,6 +186,7 @@ class SPH:
         d["sweep_ms"] = list(st.sweep_ms)
         d["sweep_launches"] = list(st.sweep_launches)
         d["sweep_units"] = list(st.sweep_units)
+        d["sweep_candidates"] = list(st.sweep_candidates)
         return d
 
     def profile(self, enable=True):
