@@ -71,17 +71,19 @@ typedef struct sph_params {
   float gamma;          /* adiabatic index, P = (gamma-1) rho u; 5/3 */
   int32_t split_count;  /* split a cell holding more than this many particles ... ; 300 */
   float split_frac;     /* ... when more than this fraction have h <= edge/2; 0.875 */
-  int32_t block_max;    /* largest particle block a warp owns in a sweep (32..256); 128 */
+  int32_t block_max;    /* largest particle block (sort unit; a warp sweeps it in chunks of 32) (32..256); 64 */
   int32_t max_newton;   /* h iterations per solve; 64 */
   int32_t max_rebuild;  /* decomposition rebuilds when a solved h outgrows its cell; 4 */
   int32_t kahan;        /* 1: compensated (Neumaier) sums across interaction tasks; 0: plain FP32 */
   int32_t morton_bits;  /* octree depth limit below the box, bits per axis (8..20); 16 */
   float h_tol;          /* converged when |N - n_ngb| <= h_tol * n_ngb; 2^-19 */
-  int32_t warps_per_cta;/* sweep kernels: warps per CTA (1..8); 4 */
+  int32_t warps_per_cta;/* sweep kernels: warps per CTA (1..8); 8 */
   int32_t ctas_per_sm;  /* sweep kernels: resident CTAs per SM used to size the persistent grid; 0 = occupancy */
   int32_t h_est_mode;   /* h estimate when no guess is given: 0 density of the leaf's parent,
                            1 the lower of leaf and parent densities; 1 */
   float h_est_factor;   /* multiplies the estimated h (a margin against rebuilds); 1.5 */
+  int32_t sweep_cap;    /* sweep kernels: j-particles a warp buffers in shared memory between
+                           compute passes (multiple of 32, 32..1024); 128 */
 } sph_params;
 
 /* Statistics of the last build and sweeps (host copy). */

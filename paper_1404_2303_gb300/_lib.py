@@ -26,7 +26,7 @@ class SphParams(C.Structure):
         ("split_frac", C.c_float), ("block_max", C.c_int32), ("max_newton", C.c_int32),
         ("max_rebuild", C.c_int32), ("kahan", C.c_int32), ("morton_bits", C.c_int32),
         ("h_tol", C.c_float), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
-        ("h_est_mode", C.c_int32), ("h_est_factor", C.c_float),
+        ("h_est_mode", C.c_int32), ("h_est_factor", C.c_float), ("sweep_cap", C.c_int32),
     ]
 
 

@@ -246,16 +246,17 @@ void sph_default_params(sph_params* p) {
   p->gamma = 5.0f / 3.0f;
   p->split_count = 300;
   p->split_frac = 0.875f;
-  p->block_max = 128;
+  p->block_max = 64;
   p->max_newton = 64;
   p->max_rebuild = 4;
   p->kahan = 1;
   p->morton_bits = 16;
   p->h_tol = 1.0f / 524288.0f;  // 2^-19
-  p->warps_per_cta = 4;
+  p->warps_per_cta = 8;
   p->ctas_per_sm = 0;
   p->h_est_mode = 1;
   p->h_est_factor = 1.5f;
+  p->sweep_cap = 128;
 }
 
 int sph_create(const sph_params* p, sph_ctx** out) {
@@ -267,11 +268,12 @@ int sph_create(const sph_params* p, sph_ctx** out) {
       q.block_max < 32 || q.block_max > 256 || q.max_newton < 1 || q.max_rebuild < 0 ||
       q.morton_bits < 8 || q.morton_bits > 20 || !(q.h_tol > 0.f) || q.warps_per_cta < 1 ||
       q.warps_per_cta > 8 || q.ctas_per_sm < 0 || q.h_est_mode < 0 || q.h_est_mode > 1 ||
-      !(q.h_est_factor > 0.f))
+      !(q.h_est_factor > 0.f) || q.sweep_cap < 32 || q.sweep_cap > 1024 || (q.sweep_cap % 32) != 0)
     return SPH_ERR_INVALID_ARG;
   sph_ctx* c = new sph_ctx();
   c->prm = q;
   c->kbits = q.morton_bits;
+  c->sweep_cap = q.sweep_cap;
   int r;
   if ((r = dbuf_ensure(c->status, 64)) != SPH_OK || (r = dbuf_ensure(c->counters, 64)) != SPH_OK ||
       (r = dbuf_ensure(c->queue, 64)) != SPH_OK) {

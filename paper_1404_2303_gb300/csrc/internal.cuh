@@ -152,6 +152,8 @@ struct sph_ctx {
 
   sph_stats stats{};
   int sweep_grid = 0;
+  int sweep_cap = 128;  // buffered j-particles per warp in the sweeps
+  bool dir_table_set = false;
   int sweep_threads = 0;
   // profiling: (phase, start, stop) events recorded around sweep launches
   bool profile = false;

@@ -1,19 +1,24 @@
 // Interaction sweeps: the sorted cell-pair interactions of Section 3.3 run
-// as persistent warps.  A warp owns one particle block (a leaf cell or a
-// slice of a large leaf) and walks the block's directed interaction list:
-// its own leaf (the self interaction, swept inside a two-sided window along
-// one axis) and every cell it shares a final pair task with (the pair
-// interaction, swept from the interface along the 13-direction sort axis
-// with the axial cutoff of the paper's sorted loop).  Each particle's sums
-// stay with the warp that owns it, so no atomics touch the accumulators;
-// each pair is evaluated from both sides instead of being updated
-// symmetrically under the task conflicts of Section 3.4.
+// as persistent warps.  A warp takes one particle block (a leaf cell or a
+// slice of a large leaf) from an LPT-ordered queue and walks the block's
+// directed interaction list: its own leaf (the self interaction, swept in
+// a two-sided window along sort axis 0) and every cell it shares a final
+// pair task with (the pair interaction, swept from the interface along the
+// pair's sort axis, one of 13, up to the axial cutoff of the paper's sorted
+// loop).  Each particle's sums stay in the registers of the lane that owns
+// it, so no atomics touch the accumulators; each pair is evaluated from
+// both sides instead of being updated symmetrically under the task
+// conflicts of Section 3.4.
 //
-// Per chunk of 32 i-particles (consecutive in the block's sorted order, so
-// their axial windows nearly coincide) the j-particles inside the chunk's
-// window are staged 32 at a time in shared memory and every lane evaluates
-// every staged j (branch-free: the cubic spline's clamps zero everything
-// beyond the support).
+// Per chunk of 32 block particles (one per lane, consecutive in Morton
+// order, so spatially compact) the warp first gathers: for every task it
+// projects its particles on the task's sort axis, takes the chunk's axial
+// window, and appends the j-particles inside it (shifted into the block's
+// frame) to a shared-memory buffer.  When the buffer is full the warp
+// computes: every lane evaluates every buffered j branch-free (the cubic
+// spline's clamps zero everything beyond the support), then folds the
+// buffer's partial sums into its running sums with a compensated
+// (Neumaier) addition.
 #include <algorithm>
 #include <cfloat>
 
@@ -46,27 +51,11 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return r;
 }
 
-// first index in the ascending keys[0, n) with keys[i] >= v (warp-wide)
-__device__ __forceinline__ int warp_lower_bound(const float* keys, int n, float v) {
-  const int lane = threadIdx.x & 31;
-  int lo = 0, hi = n;
-  while (hi - lo > 32) {
-    int step = (hi - lo + 31) >> 5;
-    int pos = lo + lane * step;
-    bool less = pos < hi && keys[pos] < v;
-    int c = __popc(__ballot_sync(FULL, less));
-    int nlo = c > 0 ? lo + (c - 1) * step + 1 : lo;
-    int nhi = min(hi, lo + c * step);
-    lo = nlo;
-    hi = nhi;
-  }
-  int pos = lo + lane;
-  bool less = pos < hi && keys[pos] < v;
-  return lo + __popc(__ballot_sync(FULL, less));
-}
+__constant__ float c_dir[SPH_NDIR][3];
 
 struct SweepArgs {
   int nblock;
+  int cap;  // buffered j-particles per warp between two compute passes
   const int* order;
   const int* b_first;
   const int* b_count;
@@ -90,7 +79,6 @@ struct SweepArgs {
   int* status;
   float delta;
   int kahan;
-  int bmax;
   // outputs (cell order)
   float* o0;
   float* o1;
@@ -132,14 +120,12 @@ struct PDensity {
     i.x = i.y = i.z = 0.f;
     i.h = 0.f; i.hinv = 0.f; i.h2 = 0.f;
   }
-  __device__ static float cut(const I& i, float) { return i.h; }
-  __device__ static float maxcut(float hb, float) { return hb; }
-  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
-    float4 q = a.pos4[j];
-    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
+  __device__ static float cut_h(float h, float) { return h; }
+  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+    tile[lane] = pj;
   }
   template <bool COUNT>
-  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
     float4 p = tile[t];
     float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
@@ -175,13 +161,12 @@ struct PDensityD2 {
   using I = PDensity::I;
   __device__ static void load_i(const SweepArgs& a, int p, I& i) { PDensity::load_i(a, p, i); }
   __device__ static void null_i(I& i) { PDensity::null_i(i); }
-  __device__ static float cut(const I& i, float) { return i.h; }
-  __device__ static float maxcut(float hb, float) { return hb; }
-  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
-    PDensity::stage(a, j, sh, tile, lane);
+  __device__ static float cut_h(float h, float) { return h; }
+  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+    PDensity::stage(a, j, pj, tile, lane, cap);
   }
   template <bool COUNT>
-  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
     float4 p = tile[t];
     float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
@@ -232,20 +217,18 @@ struct PForce {
     i.h = i.hinv = i.h2 = i.C = 0.f;
     i.p = -1;
   }
-  __device__ static float cut(const I& i, float hj) { return fmaxf(i.h, hj); }
-  __device__ static float maxcut(float hb, float hj) { return fmaxf(hb, hj); }
-  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
-    float4 q = a.pos4[j];
-    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
-    tile[32 + lane] = a.vel4[j];
+  __device__ static float cut_h(float h, float hj) { return fmaxf(h, hj); }
+  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+    tile[lane] = pj;
+    tile[cap + lane] = a.vel4[j];
     float4 f = a.fdat[j];
-    tile[64 + lane] = make_float4(f.x, f.y, f.z, __int_as_float(j));
+    tile[2 * cap + lane] = make_float4(f.x, f.y, f.z, __int_as_float(j));
   }
   template <bool COUNT>
-  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
     float4 p = tile[t];
-    float4 v = tile[32 + t];
-    float4 f = tile[64 + t];
+    float4 v = tile[cap + t];
+    float4 f = tile[2 * cap + t];
     float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
@@ -302,19 +285,17 @@ struct PForceAdj {
     i.x = i.y = i.z = i.m = i.vx = i.vy = i.vz = i.h = i.hinv = i.A = 0.f;
     i.ax = i.ay = i.az = i.ub = 0.f;
   }
-  __device__ static float cut(const I& i, float hj) { return fmaxf(i.h, hj); }
-  __device__ static float maxcut(float hb, float hj) { return fmaxf(hb, hj); }
-  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
-    float4 q = a.pos4[j];
-    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
-    tile[32 + lane] = a.vel4[j];
-    tile[64 + lane] = a.adj4[j];
-    tile[96 + lane] = make_float4(a.fdat[j].w, 0.f, 0.f, 0.f);
+  __device__ static float cut_h(float h, float hj) { return fmaxf(h, hj); }
+  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+    tile[lane] = pj;
+    tile[cap + lane] = a.vel4[j];
+    tile[2 * cap + lane] = a.adj4[j];
+    tile[3 * cap + lane] = make_float4(a.fdat[j].w, 0.f, 0.f, 0.f);
   }
   template <bool COUNT>
-  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
-    float4 p = tile[t], v = tile[32 + t], g = tile[64 + t];
-    float Aj = tile[96 + t].x;
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
+    float4 p = tile[t], v = tile[cap + t], g = tile[2 * cap + t];
+    float Aj = tile[3 * cap + t].x;
     float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
@@ -388,17 +369,15 @@ struct PDensityAdj {
   __device__ static void null_i(I& i) {
     i.x = i.y = i.z = i.m = i.h = i.hinv = i.R = i.S = i.L = 0.f;
   }
-  __device__ static float cut(const I& i, float hj) { return fmaxf(i.h, hj); }
-  __device__ static float maxcut(float hb, float hj) { return fmaxf(hb, hj); }
-  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
-    float4 q = a.pos4[j];
-    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
-    tile[32 + lane] = a.adj4[j];
-    tile[64 + lane] = a.adj4b[j];
+  __device__ static float cut_h(float h, float hj) { return fmaxf(h, hj); }
+  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+    tile[lane] = pj;
+    tile[cap + lane] = a.adj4[j];
+    tile[2 * cap + lane] = a.adj4b[j];
   }
   template <bool COUNT>
-  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
-    float4 p = tile[t], u = tile[32 + t], w = tile[64 + t];
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
+    float4 p = tile[t], u = tile[cap + t], w = tile[2 * cap + t];
     float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
@@ -453,19 +432,17 @@ struct PDump {
     i.p = -1;
     i.a = nullptr;
   }
-  __device__ static float cut(const I& i, float hj) { return FORCE ? fmaxf(i.h, hj) : i.h; }
-  __device__ static float maxcut(float hb, float hj) { return FORCE ? fmaxf(hb, hj) : hb; }
-  __device__ static void stage(const SweepArgs& a, int j, float4 sh, float4* tile, int lane) {
-    float4 q = a.pos4[j];
+  __device__ static float cut_h(float h, float hj) { return FORCE ? fmaxf(h, hj) : h; }
+  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
     float h = a.h[j];
-    tile[lane] = make_float4(__fadd_rn(q.x, sh.x), __fadd_rn(q.y, sh.y), __fadd_rn(q.z, sh.z), q.w);
-    tile[32 + lane] = make_float4(__fmul_rn(h, h), __int_as_float(j), 0.f, 0.f);
+    tile[lane] = pj;
+    tile[cap + lane] = make_float4(__fmul_rn(h, h), __int_as_float(j), 0.f, 0.f);
   }
   template <bool COUNT>
-  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt) {
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
     if (i.p < 0) return;
     float4 p = tile[t];
-    float4 e = tile[32 + t];
+    float4 e = tile[cap + t];
     float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
     float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     int j = __float_as_int(e.y);
@@ -487,16 +464,52 @@ struct PDump {
 // ---------------------------------------------------------------------------
 // the generic persistent sweep
 // ---------------------------------------------------------------------------
+template <class P>
+__device__ __forceinline__ void fold(float* acc, float* cmp, float* part, int kahan) {
+#pragma unroll
+  for (int k = 0; k < P::NACC; ++k) {
+    float x = part[k];
+    if (kahan) {
+      float S = acc[k];
+      float T = S + x;
+      cmp[k] += fabsf(S) >= fabsf(x) ? (S - T) + x : (x - T) + S;
+      acc[k] = T;
+    } else {
+      acc[k] += x;
+    }
+    part[k] = 0.f;
+  }
+}
+
+template <class P, bool COUNT>
+__device__ __forceinline__ void compute_pass(const typename P::I& I, const float4* buf, int staged,
+                                             int cap, float* part, int& cnt) {
+  __syncwarp();
+#pragma unroll 2
+  for (int t = 0; t < staged; ++t) P::template interact<COUNT>(I, buf, t, part, cnt, cap);
+  __syncwarp();
+}
+
+// first index in [0, n) whose predicate flips from true to false, for a
+// predicate true on a prefix (binary search, one lane)
+#define SPH_PARTITION(n, pred_of_mid, out)       \
+  do {                                           \
+    int lo_ = 0, hi_ = (n);                      \
+    while (lo_ < hi_) {                          \
+      int mid = (lo_ + hi_) >> 1;                \
+      if (pred_of_mid) lo_ = mid + 1; else hi_ = mid; \
+    }                                            \
+    (out) = lo_;                                 \
+  } while (0)
+
 template <class P, bool COUNT>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int KS = a.kahan ? 2 : 1;
-  const int accf = a.bmax * P::NACC * KS;
-  const int per_warp = 32 * P::JW + (accf + a.bmax + 3) / 4;
-  float4* tile = smem + warp * per_warp;
-  float* acc = reinterpret_cast<float*>(tile + 32 * P::JW);
-  int* cacc = reinterpret_cast<int*>(acc + accf);
+  const int cap = a.cap;
+  float4* buf = smem + (size_t)warp * (cap * P::JW + 32);
+  float4* cpos = buf + cap * P::JW;  // the chunk's particles (x, y, z, h)
+  const unsigned lt = (1u << lane) - 1u;
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(a.queue, 1);
@@ -505,137 +518,159 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     const int b = a.order[q];
     if (a.blk_active && a.blk_active[b] == 0) continue;
     const int bf = a.b_first[b], bn = a.b_count[b];
-    for (int k = lane; k < bn * P::NACC * KS; k += 32) acc[k] = 0.f;
-    if (COUNT)
-      for (int k = lane; k < bn; k += 32) cacc[k] = 0;
-    float hb = 0.f;
-    for (int k = lane; k < bn; k += 32) hb = fmaxf(hb, a.h[bf + k]);
-    hb = warp_max(hb);
-    __syncwarp();
-    const long long e1 = a.b_dtoff[b + 1];
-    for (long long e = a.b_dtoff[b]; e < e1; ++e) {
-      const int cj = a.dt_cj[e];
-      const int code = a.dt_code[e];
-      const float4 sh = a.dt_shift[e];
-      const int dir = code & 255, sgn = (code >> 8) - 1;
-      float ux, uy, uz;
-      dir_unit(dir, ux, uy, uz);
-      const float ksh = sort_key(sh.x, sh.y, sh.z, ux, uy, uz);
-      const int ncj = a.n_count[cj];
-      const long long jb = a.n_sbase[cj] + (long long)dir * ncj;
-      const long long ib = 13ll * bf + (long long)dir * bn;
-      const float hj = P::USES_HJ ? a.n_hmax[cj] : 0.f;
-      const float maxcut = P::maxcut(hb, hj) + a.delta;
-      float knear = 0.f;  // s * key of the j nearest to the interface
-      if (sgn > 0) knear = a.s_key[jb] + ksh;
-      else if (sgn < 0) knear = -(a.s_key[jb + ncj - 1] + ksh);
-      for (int c0 = 0; c0 < bn; c0 += 32) {
-        const int t = c0 + lane;
-        const bool vi = t < bn;
-        const int ii = sgn > 0 ? bn - 1 - t : t;
-        int pi = 0;
-        float ki = 0.f;
-        typename P::I I;
-        if (vi) {
-          pi = a.s_idx[ib + ii];
-          ki = a.s_key[ib + ii];
-          P::load_i(a, pi, I);
-        } else {
-          P::null_i(I);
-        }
-        const float cut = P::cut(I, hj);
-        float accr[P::NACC];
+    const long long e0 = a.b_dtoff[b], e1 = a.b_dtoff[b + 1];
+    for (int c0 = 0; c0 < bn; c0 += 32) {
+      const int nc = min(32, bn - c0);
+      const bool vi = lane < nc;
+      const int pi = bf + c0 + (vi ? lane : 0);
+      typename P::I I;
+      if (vi) P::load_i(a, pi, I); else P::null_i(I);
+      // chunk geometry: positions, bounding box, largest h
+      {
+        float4 me = make_float4(I.x, I.y, I.z, vi ? I.h : 0.f);
+        float4 l0 = make_float4(__shfl_sync(FULL, me.x, 0), __shfl_sync(FULL, me.y, 0),
+                                __shfl_sync(FULL, me.z, 0), 0.f);
+        if (!vi) me = l0;
+        cpos[lane] = me;
+      }
+      const float bx0 = warp_min(cpos[lane].x), bx1 = warp_max(cpos[lane].x);
+      const float by0 = warp_min(cpos[lane].y), by1 = warp_max(cpos[lane].y);
+      const float bz0 = warp_min(cpos[lane].z), bz1 = warp_max(cpos[lane].z);
+      const float hmx = warp_max(vi ? I.h : 0.f);
+      __syncwarp();
+      float acc[P::NACC], cmp[P::NACC], part[P::NACC];
 #pragma unroll
-        for (int k = 0; k < P::NACC; ++k) accr[k] = 0.f;
-        int cnt = 0;
-        int jstart = 0;
-        int ncand = 0;
-        float U;
-        if (sgn != 0) {
-          const float ski = sgn > 0 ? ki : -ki;
-          U = warp_max(vi ? ski + cut + a.delta : -FLT_MAX);
-          const float near_i = __shfl_sync(FULL, ski, 0);
-          if (knear > near_i + maxcut) break;
-          if (knear > U) continue;
-        } else {
-          const float lo = warp_min(vi ? ki - cut - a.delta : FLT_MAX);
-          U = warp_max(vi ? ki + cut + a.delta : -FLT_MAX);
-          jstart = warp_lower_bound(a.s_key + jb, ncj, lo);
+      for (int k = 0; k < P::NACC; ++k) acc[k] = cmp[k] = part[k] = 0.f;
+      int cnt = 0, ncand = 0, staged = 0;
+      for (long long g = e0; g < e1; g += 32) {
+        // ---- one lane per interaction task: window of the chunk in the
+        // task cell's sorted list (the axial cutoff of the sorted sweep)
+        const long long e = g + lane;
+        const bool ve = e < e1;
+        int cj = 0, code = 1 << 8, ncj = 0;
+        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+        long long jb = 0;
+        float hj = 0.f;
+        if (ve) {
+          cj = a.dt_cj[e];
+          code = a.dt_code[e];
+          sh = a.dt_shift[e];
+          ncj = a.n_count[cj];
+          jb = a.n_sbase[cj];
+          if (P::USES_HJ) hj = a.n_hmax[cj];
         }
-        for (int j0 = jstart; j0 < ncj; j0 += 32) {
-          const int jj = j0 + lane;
-          const bool vj = jj < ncj;
-          const long long jp = jb + (sgn >= 0 ? jj : ncj - 1 - jj);
-          float sk = FLT_MAX;
-          if (vj) {
-            float kj = a.s_key[jp] + ksh;
-            sk = sgn >= 0 ? kj : -kj;
-          }
-          const bool in = vj && sk <= U;
-          const int nv = __popc(__ballot_sync(FULL, in));
-          if (in) P::stage(a, a.s_idx[jp], sh, tile, lane);
-          __syncwarp();
-          for (int t2 = 0; t2 < nv; ++t2) P::template interact<COUNT>(I, tile, t2, accr, cnt);
-          if (COUNT && vi) ncand += nv;
-          __syncwarp();
-          if (nv < 32) break;
+        const int dir = code & 255, sgn = (code >> 8) - 1;
+        jb += (long long)dir * ncj;
+        const float ux = c_dir[dir][0], uy = c_dir[dir][1], uz = c_dir[dir][2];
+        const float ksh = sgn != 0 ? sort_key(sh.x, sh.y, sh.z, ux, uy, uz) : 0.f;
+        float U = -FLT_MAX, L = FLT_MAX;
+        for (int p = 0; p < nc; ++p) {
+          const float4 c = cpos[p];
+          const float k = sort_key(c.x, c.y, c.z, ux, uy, uz);
+          const float ct = P::cut_h(c.w, hj) + a.delta;
+          const float sk = sgn < 0 ? -k : k;
+          U = fmaxf(U, sk + ct);
+          L = fminf(L, k - ct);
         }
-        if (vi) {
-          float* s = acc + (pi - bf) * P::NACC * KS;
-          if (KS == 2) {
-#pragma unroll
-            for (int k = 0; k < P::NACC; ++k) {
-              float S = s[2 * k], Cc = s[2 * k + 1], x = accr[k];
-              float T = S + x;
-              Cc += fabsf(S) >= fabsf(x) ? (S - T) + x : (x - T) + S;
-              s[2 * k] = T;
-              s[2 * k + 1] = Cc;
-            }
+        int js = 0, jn = 0;
+        if (ve && ncj > 0) {
+          const float* K = a.s_key + jb;
+          if (sgn > 0) {
+            SPH_PARTITION(ncj, K[mid] + ksh <= U, jn);
+          } else if (sgn < 0) {
+            SPH_PARTITION(ncj, -(K[mid] + ksh) > U, js);
+            jn = ncj - js;
           } else {
-#pragma unroll
-            for (int k = 0; k < P::NACC; ++k) s[k] += accr[k];
+            int je;
+            SPH_PARTITION(ncj, K[mid] < L, js);
+            SPH_PARTITION(ncj, K[mid] <= U, je);
+            jn = max(je - js, 0);
           }
-          if (COUNT) cacc[pi - bf] += cnt;
         }
-        if (COUNT && a.units) {
+        const float C = (P::USES_HJ ? fmaxf(hmx, hj) : hmx) + a.delta;
+        const float C2 = C * C;
+        int incl = jn;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(FULL, ncand, o);
-          if (lane == 0) atomicAdd(a.units + 1, (unsigned long long)ncand);
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int excl = incl - jn;
+        const int total = __shfl_sync(FULL, incl, 31);
+        // ---- flat gather over every window, filtered by the chunk's box
+        for (int f0 = 0; f0 < total; f0 += 32) {
+          const int f = f0 + lane;
+          int k = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            int v = __shfl_sync(FULL, excl, k + step);
+            if (v <= f) k += step;
+          }
+          const long long jbk = __shfl_sync(FULL, jb, k);
+          const int jsk = __shfl_sync(FULL, js, k);
+          const int exk = __shfl_sync(FULL, excl, k);
+          const float sx = __shfl_sync(FULL, sh.x, k), sy = __shfl_sync(FULL, sh.y, k),
+                      sz = __shfl_sync(FULL, sh.z, k);
+          const float Ck2 = __shfl_sync(FULL, C2, k);
+          bool take = false;
+          int jidx = 0;
+          float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (f < total) {
+            jidx = a.s_idx[jbk + jsk + (f - exk)];
+            const float4 q = a.pos4[jidx];
+            pj = make_float4(__fadd_rn(q.x, sx), __fadd_rn(q.y, sy), __fadd_rn(q.z, sz), q.w);
+            const float dx = fmaxf(fmaxf(bx0 - pj.x, pj.x - bx1), 0.f);
+            const float dy = fmaxf(fmaxf(by0 - pj.y, pj.y - by1), 0.f);
+            const float dz = fmaxf(fmaxf(bz0 - pj.z, pj.z - bz1), 0.f);
+            take = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= Ck2;
+          }
+          const unsigned mt = __ballot_sync(FULL, take);
+          const int nt = __popc(mt);
+          if (staged + nt > cap) {
+            compute_pass<P, COUNT>(I, buf, staged, cap, part, cnt);
+            if (COUNT && vi) ncand += staged;
+            fold<P>(acc, cmp, part, a.kahan);
+            staged = 0;
+          }
+          if (take) P::stage(a, jidx, pj, buf, staged + __popc(mt & lt), cap);
+          staged += nt;
+        }
+      }
+      compute_pass<P, COUNT>(I, buf, staged, cap, part, cnt);
+      if (COUNT && vi) ncand += staged;
+      fold<P>(acc, cmp, part, a.kahan);
+      if (vi) {
+        float v[P::NACC];
+#pragma unroll
+        for (int k = 0; k < P::NACC; ++k) v[k] = acc[k] + cmp[k];
+        P::finalize(a, pi, v);
+        if (COUNT && a.ocnt) a.ocnt[pi] = cnt;
+      }
+      if (COUNT && a.units) {
+        int ct = vi ? cnt : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ct += __shfl_xor_sync(FULL, ct, o);
+          ncand += __shfl_xor_sync(FULL, ncand, o);
+        }
+        if (lane == 0) {
+          atomicAdd(a.units, (unsigned long long)ct);
+          atomicAdd(a.units + 1, (unsigned long long)ncand);
         }
       }
       __syncwarp();
     }
-    __syncwarp();
-    int btot = 0;
-    for (int k = lane; k < bn; k += 32) {
-      float v[P::NACC];
-      const float* s = acc + k * P::NACC * KS;
-#pragma unroll
-      for (int m = 0; m < P::NACC; ++m) v[m] = KS == 2 ? s[2 * m] + s[2 * m + 1] : s[m];
-      P::finalize(a, bf + k, v);
-      if (COUNT) {
-        if (a.ocnt) a.ocnt[bf + k] = cacc[k];
-        btot += cacc[k];
-      }
-    }
-    if (COUNT && a.units) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) btot += __shfl_xor_sync(FULL, btot, o);
-      if (lane == 0) atomicAdd(a.units, (unsigned long long)btot);
-    }
-    __syncwarp();
   }
 }
 
 template <class P, bool COUNT>
 int launch(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
   const int warps = c->prm.warps_per_cta;
-  const int KS = a.kahan ? 2 : 1;
-  const int accf = a.bmax * P::NACC * KS;
-  const int per_warp = 32 * P::JW + (accf + a.bmax + 3) / 4;
-  size_t smem = (size_t)warps * per_warp * sizeof(float4);
+  a.cap = c->sweep_cap;
+  size_t smem = (size_t)warps * (a.cap * P::JW + 32) * sizeof(float4);
   auto kern = k_sweep<P, COUNT>;
-  if (smem > 48 * 1024) SPH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024)
+    SPH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, nsm = 0, per_sm = c->prm.ctas_per_sm;
   SPH_CUDA(cudaGetDevice(&dev));
   SPH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -708,6 +743,12 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   if (c->nblock == 0) return SPH_OK;
   c->cur_phase = phase;
   if (c->profile && phase < PH_DUMP_DENSITY) counting = 1;
+  if (!c->dir_table_set) {
+    float t[SPH_NDIR][3];
+    for (int d = 0; d < SPH_NDIR; ++d) dir_unit(d, t[d][0], t[d][1], t[d][2]);
+    SPH_CUDA(cudaMemcpyToSymbolAsync(c_dir, t, sizeof(t), 0, cudaMemcpyHostToDevice, s));
+    c->dir_table_set = true;
+  }
   SweepArgs a{};
   a.nblock = c->nblock;
   a.order = c->b_order.as<int>();
@@ -733,7 +774,6 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   for (int b = 0; b < c->nbox; ++b) emax = std::max(emax, c->box_L[b] / (double)(1 << c->box_t[b]));
   a.delta = (float)(emax * (1.0 / 65536.0));
   a.kahan = c->prm.kahan ? 1 : 0;
-  a.bmax = c->prm.block_max;
   a.ocnt = counting ? c->cnt_i.as<int>() : nullptr;
   switch (phase) {
     case PH_DENSITY:
