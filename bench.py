@@ -40,6 +40,8 @@ LANES = 128
 
 
 def workload(name):
+    """The synthetic workloads (synth/configs.py); batched ones carry
+    'offsets' / 'boxes' for sph_build_batch."""
     import synth.configs as C
     if name == "multires128":
         return C.multires(128, seed=2)
@@ -49,6 +51,12 @@ def workload(name):
         return C.uniform_lattice(16, seed=1)
     if name == "sinusoid64":
         return C.sinusoid(64, seed=4)
+    if name == "batch64":
+        return C.concat_boxes(C.batch_boxes(64, seed=3))
+    if name == "lognormal256":
+        return C.lognormal(256, seed=5, sigma=4.0)
+    if name == "zeldovich256":
+        return C.zeldovich(256, seed=5, amp=8.0)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -120,12 +128,19 @@ def oracle_sample_rate(d, seconds_target=15.0, seed=0, sample=None):
     units of the sampled particles (their directed density interactions
     plus half their force partners) per second of oracle time."""
     from oracle import sph_oracle as O
-    n = d["x"].shape[0]
     rng = np.random.default_rng(seed)
     S = sample or 256
+    x, m, u, v = d["x"], d["m"], d["u"], d["v"]
+    if "offsets" in d:  # independent boxes: sample inside one of them
+        off = d["offsets"]
+        b = int(rng.integers(len(off) - 1))
+        sl = slice(off[b], off[b + 1])
+        x, m, u, v = x[sl], m[sl], u[sl], v[sl]
+    n = x.shape[0]
+    S = min(S, n)
     idx = np.sort(rng.choice(n, S, replace=False))
     t0 = time.perf_counter()
-    r = O.evaluate_sample(d["x"], d["m"], d["u"], idx, v=d["v"])
+    r = O.evaluate_sample(x, m, u, idx, v=v)
     dt = time.perf_counter() - t0
     units = float(np.sum(r["count"]) + 0.5 * np.sum(r["force_count"]))
     return dict(value=units / dt, seconds=dt, sample=int(S), units=units)
@@ -209,11 +224,16 @@ def main():
 
     ev = {}
 
+    batched = "offsets" in d
+
     def step(pos, m, u, vel, mark=False):
         if mark:
             ev.setdefault("f0", []).append(torch.cuda.Event(enable_timing=True))
             ev["f0"][-1].record(stream)
-        sph.build(pos)
+        if batched:
+            sph.build_batch(pos, d["offsets"], d["boxes"])
+        else:
+            sph.build(pos)
         den = sph.density(m)
         acc, dudt, _ = sph.force(u, vel)
         if mark:

@@ -81,7 +81,8 @@ typedef struct sph_params {
   int32_t ctas_per_sm;  /* sweep kernels: resident CTAs per SM used to size the persistent grid; 0 = occupancy */
   int32_t h_est_mode;   /* h estimate when no guess is given: 0 density of the leaf's parent,
                            1 the lower of leaf and parent densities; 1 */
-  float h_est_factor;   /* multiplies the estimated h (a margin against rebuilds); 1.5 */
+  float h_est_factor;   /* the cells are built for the estimate times this margin (fewer
+                           rebuilds); the solve starts from the estimate itself; 1.5 */
   int32_t sweep_cap;    /* sweep kernels: j-particles a warp buffers in shared memory between
                            compute passes (multiple of 32, 32..1024); 128 */
 } sph_params;
@@ -110,6 +111,9 @@ typedef struct sph_stats {
   int64_t sweep_units[8];    /* pairs accepted by those launches: directed (i<-j) for
                                 phases 0 and 1, ordered i != j pairs for 2..4 */
   int64_t sweep_candidates[8]; /* (i, j) candidates those launches evaluated */
+  int32_t newton_active[32]; /* particles still iterating after each of the first 32 h iterations
+                                of the last solve round (0 afterwards) */
+  int32_t unconverged;       /* particles left unconverged by the last sph_density */
   int32_t sweep_grid;        /* CTAs of the last sweep launch */
   int32_t sweep_threads;     /* threads per CTA of the sweep launches */
 } sph_stats;

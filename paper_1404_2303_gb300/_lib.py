@@ -37,7 +37,8 @@ class SphStats(C.Structure):
         ("max_depth", C.c_int32), ("top_level", C.c_int32 * 8), ("newton_iters", C.c_int32),
         ("rebuilds", C.c_int32), ("density_interactions", C.c_int64), ("force_pairs", C.c_int64),
         ("sorted_entries", C.c_int64), ("sweep_ms", C.c_double * 8),
-        ("sweep_launches", C.c_int32 * 8), ("sweep_units", C.c_int64 * 8), ("sweep_candidates", C.c_int64 * 8), ("sweep_grid", C.c_int32), ("sweep_threads", C.c_int32),
+        ("sweep_launches", C.c_int32 * 8), ("sweep_units", C.c_int64 * 8), ("sweep_candidates", C.c_int64 * 8),
+        ("newton_active", C.c_int32 * 32), ("unconverged", C.c_int32), ("sweep_grid", C.c_int32), ("sweep_threads", C.c_int32),
     ]
 
 

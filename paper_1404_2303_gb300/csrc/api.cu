@@ -41,9 +41,15 @@ __global__ void k_check_h(long long n, const float* h, const float* hlim, int* s
   if (!(v > 0.f) || v > hlim[s]) atomicOr(status, ST_CELL_LIMIT);
 }
 
-// ---- smoothing-length solve (Eq. (nneigh)): FP64 bracket, Newton steps
+// ---- smoothing-length solve (Eq. (nneigh)): Newton steps on
+// ln N(ln h) = ln n_ngb (the paper's Newton iteration with dN/dh computed
+// alongside the sums, taken in log-log form so that it lands on the root in
+// one step when N grows like h^3), safeguarded by an FP64 bracket [lo, hi]:
+// a step that leaves the bracket, or that is not at least twice shorter than
+// the step before it, is replaced by bisection, so the bracket keeps
+// shrinking even where N(h) is steep.
 __global__ void k_hsolve_init(long long n, float* h, const float* hlim, double* lo, double* hi,
-                              int* flag) {
+                              float* dxold, int* flag) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
   float hl = hlim[s];
@@ -52,24 +58,26 @@ __global__ void k_hsolve_init(long long n, float* h, const float* hlim, double* 
   h[s] = v;
   lo[s] = 0.0;
   hi[s] = (double)hl;
+  dxold[s] = 1e30f;
   flag[s] = HF_ACTIVE;
 }
 
 __global__ void k_hsolve_update(long long n, float* h, const float* hlim, const float* nngb,
-                                const float* dnngb, double* lo, double* hi, int* flag, float n_ngb,
-                                float tol, int* nactive, int* nlimit) {
+                                const float* dnngb, double* lo, double* hi, float* dxold, int* flag,
+                                float n_ngb, float tol, int* nactive, int* nlimit) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int fl = flag[s];
   if (!(fl & HF_ACTIVE)) return;
-  double hd = (double)h[s];
-  double f = (double)nngb[s] - (double)n_ngb;
+  const double hd = (double)h[s];
+  const float Nv = nngb[s];
+  const double f = (double)Nv - (double)n_ngb;
   if (fabs(f) <= (double)tol * (double)n_ngb) {
     flag[s] = fl & ~HF_ACTIVE;
     return;
   }
   double L = lo[s], H = hi[s];
-  double hl = (double)hlim[s];
+  const double hl = (double)hlim[s];
   if (f < 0) {
     L = hd;
     if (hd >= hl) {  // the root lies beyond what this decomposition covers
@@ -81,17 +89,23 @@ __global__ void k_hsolve_update(long long n, float* h, const float* hlim, const 
     H = hd;
     fl |= HF_HI_VALID;
   }
-  // Newton step on ln N(ln h) = ln n_ngb: the same derivative dN/dh, taken
-  // in log-log form, lands on the root in one step when N grows like h^3
-  double dN = (double)dnngb[s];
-  double Nv = (double)nngb[s];
-  double slope = (dN > 0 && Nv > 0) ? hd * dN / Nv : 0.0;
-  // (FP32 transcendentals: the step is only a proposal inside the FP64 bracket)
-  double hn = slope > 1e-3
-                  ? hd * (double)__expf((__logf(n_ngb) - __logf((float)Nv)) / (float)slope)
-                  : -1.0;
+  // Newton step in x = ln h on g(x) = ln N - ln n_ngb, g'(x) = h N'/N
+  const float slope = (dnngb[s] > 0.f && Nv > 0.f) ? (float)(hd * (double)dnngb[s] / (double)Nv) : 0.f;
+  const float g = __logf(Nv) - __logf(n_ngb);
+  const float dx = slope > 1e-3f ? g / slope : 0.f;  // ln(h / h_new)
+  double hn;
+  float step;
   if (fl & HF_HI_VALID) {
-    if (!(hn > L && hn < H)) hn = 0.5 * (L + H);
+    const double prop = slope > 1e-3f ? hd * (double)__expf(-dx) : -1.0;
+    const bool out = !(prop > L && prop < H);
+    const bool slow = fabsf(2.f * g) > fabsf(dxold[s] * slope);
+    if (out || slow || slope <= 1e-3f) {
+      hn = L > 0 ? sqrt(L * H) : 0.5 * (L + H);  // bisection (geometric once L > 0)
+      step = (float)fabs(log(hn / hd));
+    } else {
+      hn = prop;
+      step = fabsf(dx);
+    }
     if (H - L <= 2.4e-7 * hd) {  // bracket below FP32 resolution
       lo[s] = L;
       hi[s] = H;
@@ -99,13 +113,18 @@ __global__ void k_hsolve_update(long long n, float* h, const float* hlim, const 
       return;
     }
   } else {
+    // no upper end yet: Newton upwards, doubling when it has no slope, capped
+    // at the cell limit (evaluated there once before declaring the limit)
+    hn = slope > 1e-3f ? hd * (double)__expf(-dx) : 2.0 * hd;
     if (!(hn > L)) hn = 2.0 * hd;
     hn = fmin(hn, hl);
+    step = (float)fabs(log(hn / hd));
   }
-  float hf = (float)hn;
   lo[s] = L;
   hi[s] = H;
-  if (hf == h[s]) {
+  dxold[s] = step;
+  const float hf = (float)hn;
+  if (hf == h[s] || step < 1e-7f) {  // no FP32-representable progress left
     flag[s] = fl & ~HF_ACTIVE;
     return;
   }
@@ -222,6 +241,7 @@ static int ensure_state(sph_ctx* c) {
   SPH_TRY(dbuf_ensure(c->h_lo, 8 * n));
   SPH_TRY(dbuf_ensure(c->h_hi, 8 * n));
   SPH_TRY(dbuf_ensure(c->h_flag, 4 * n));
+  SPH_TRY(dbuf_ensure(c->h_dx, 4 * n));
   SPH_TRY(dbuf_ensure(c->blk_active, 4 * (size_t)(c->nblock + 1)));
   SPH_TRY(dbuf_ensure(c->tmp_a, 64));
   return SPH_OK;
@@ -297,7 +317,7 @@ void sph_destroy(sph_ctx* c) {
                  &c->b_dtoff, &c->b_order, &c->b_cost, &c->dt_cj, &c->dt_code, &c->dt_shift,
                  &c->adj_off, &c->adj_list, &c->s_key, &c->s_idx, &c->rho, &c->drho, &c->nngb,
                  &c->dnngb, &c->d2rho, &c->omega, &c->Avec, &c->fdat, &c->vel4, &c->u_s, &c->acc4,
-                 &c->cnt_i, &c->h_lo, &c->h_hi, &c->h_flag, &c->blk_active, &c->adj4, &c->adj4b, &c->g_A,
+                 &c->cnt_i, &c->h_lo, &c->h_hi, &c->h_dx, &c->h_flag, &c->blk_active, &c->adj4, &c->adj4b, &c->g_A,
                  &c->g_rho_s, &c->g_drho_s, &c->g_h_s, &c->g_u_s, &c->g_x4,
                  &c->prof_units, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
                  &c->tmp_b, &c->tmp_c};
@@ -403,10 +423,11 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
   for (;;) {
     { k_hsolve_init<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), c->hlim.as<float>(),
                                                  c->h_lo.as<double>(), c->h_hi.as<double>(),
-                                                 c->h_flag.as<int>()); note_launch(); }
+                                                 c->h_dx.as<float>(), c->h_flag.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
     int host[2] = {1, 0};
     int it = 0;
+    for (int k = 0; k < 32; ++k) c->stats.newton_active[k] = 0;
     SPH_CUDA(cudaMemsetAsync(c->blk_active.p, 0, 4 * (size_t)c->nblock, s));
     // nlim accumulates over the whole solve: a particle flagged at its cell
     // limit in any iteration leaves the active set and must trigger the rebuild
@@ -420,17 +441,19 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
       SPH_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), s));
       { k_hsolve_update<<<div_up(n, TPB), TPB, 0, s>>>(
           n, c->h.as<float>(), c->hlim.as<float>(), c->nngb.as<float>(), c->dnngb.as<float>(),
-          c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_flag.as<int>(), c->prm.n_ngb,
-          c->prm.h_tol, nact, nlim); note_launch(); }
+          c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_dx.as<float>(), c->h_flag.as<int>(),
+          c->prm.n_ngb, c->prm.h_tol, nact, nlim); note_launch(); }
       SPH_CUDA(cudaGetLastError());
       SPH_CUDA(cudaMemcpyAsync(host, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       SPH_CUDA(cudaStreamSynchronize(s));
+      if (it < 32) c->stats.newton_active[it] = host[0];
       if (host[0] == 0) {
         ++it;
         break;
       }
     }
     total_iters += it;
+    c->stats.unconverged = host[0];
     if (host[0] != 0) {
       c->stats.newton_iters = total_iters;
       return SPH_ERR_H_NOT_CONVERGED;

@@ -168,6 +168,11 @@ __global__ void k_h_estimate(long long n, const int* pnode, const int* parent, c
   hout[s] = (float)h;
 }
 
+__global__ void k_scale(long long n, float* v, float f) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < n) v[s] *= f;
+}
+
 __global__ void k_relpos(long long n, const unsigned long long* keys, const double* xs,
                          const double* Ls, const int* box_t, int K, float4* pos4) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1257,7 +1262,14 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
                                                 c->hguess.as<float>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
   }
-  return build_from_guess(c, s);
+  SPH_TRY(build_from_guess(c, s));
+  if (!h_guess && c->prm.h_est_factor != 1.0f) {
+    // cells were built for the widened estimate; the solve starts from the
+    // estimate itself
+    { k_scale<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), 1.0f / c->prm.h_est_factor); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  return SPH_OK;
 }
 
 int build_from_guess(sph_ctx* c, cudaStream_t s) {

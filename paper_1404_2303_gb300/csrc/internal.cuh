@@ -135,6 +135,7 @@ struct sph_ctx {
   DBuf cnt_i;     // int per-particle counts
   // h solver
   DBuf h_lo, h_hi;   // double bracket
+  DBuf h_dx;         // float previous |step| in ln h
   DBuf h_flag;       // int: bit0 active, bit1 hi evaluated, bit2 cell limit
   DBuf blk_active;   // int per block
   // adjoint state

@@ -79,6 +79,8 @@ struct SweepArgs {
   int* status;
   float delta;
   int kahan;
+  int bmax;             // largest block (particles)
+  const int* pflag;     // h iteration: per-particle flags (bit 0: still iterating)
   // outputs (cell order)
   float* o0;
   float* o1;
@@ -502,13 +504,24 @@ __device__ __forceinline__ void compute_pass(const typename P::I& I, const float
     (out) = lo_;                                 \
   } while (0)
 
+// factor-2 band of a particle's h above the block's smallest h (0..15);
+// 31 for particles that need no sweep (converged during the h iteration)
+__device__ __forceinline__ int h_class(const SweepArgs& a, int p, float hmin) {
+  if (!a.pflag) return 0;  // full sweeps keep plain Morton chunks
+  if (!(a.pflag[p] & 1)) return 31;
+  const float r = a.h[p] / hmin;
+  const int c = r < 2.f ? 0 : (int)__log2f(r);
+  return c > 15 ? 15 : c;
+}
+
 template <class P, bool COUNT>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cap = a.cap;
-  float4* buf = smem + (size_t)warp * (cap * P::JW + 32);
+  float4* buf = smem + (size_t)warp * (cap * P::JW + 32 + a.bmax / 4);
   float4* cpos = buf + cap * P::JW;  // the chunk's particles (x, y, z, h)
+  int* ord = reinterpret_cast<int*>(cpos + 32);  // the block's particles grouped by h class
   const unsigned lt = (1u << lane) - 1u;
   for (;;) {
     int q = 0;
@@ -519,10 +532,33 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     if (a.blk_active && a.blk_active[b] == 0) continue;
     const int bf = a.b_first[b], bn = a.b_count[b];
     const long long e0 = a.b_dtoff[b], e1 = a.b_dtoff[b + 1];
-    for (int c0 = 0; c0 < bn; c0 += 32) {
-      const int nc = min(32, bn - c0);
+    // During the h iteration only particles still iterating are swept, and
+    // they are grouped by h class (factor-2 bands above the block's smallest
+    // h, Morton order inside a band): chunks share one window per task, set
+    // by their largest h, so a few large-h iterates must not widen the
+    // windows of many small-h ones.  Full sweeps use plain Morton chunks.
+    float hmin = FLT_MAX;
+    for (int k = lane; k < bn; k += 32) hmin = fminf(hmin, a.h[bf + k]);
+    hmin = warp_min(hmin);
+    unsigned present = 0;
+    for (int k = lane; k < bn; k += 32) present |= 1u << h_class(a, bf + k, hmin);
+    present = __reduce_or_sync(FULL, present) & 0x7fffffffu;  // class 31: not swept
+    while (present) {
+      const int cls = __ffs(present) - 1;
+      present &= present - 1;
+      int ncls = 0;
+      for (int k0 = 0; k0 < bn; k0 += 32) {
+        const int k = k0 + lane;
+        const bool in = k < bn && h_class(a, bf + k, hmin) == cls;
+        const unsigned mk = __ballot_sync(FULL, in);
+        if (in) ord[ncls + __popc(mk & lt)] = k;
+        ncls += __popc(mk);
+      }
+      __syncwarp();
+    for (int c0 = 0; c0 < ncls; c0 += 32) {
+      const int nc = min(32, ncls - c0);
       const bool vi = lane < nc;
-      const int pi = bf + c0 + (vi ? lane : 0);
+      const int pi = bf + ord[c0 + (vi ? lane : 0)];
       typename P::I I;
       if (vi) P::load_i(a, pi, I); else P::null_i(I);
       // chunk geometry: positions, bounding box, largest h
@@ -622,7 +658,13 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
             const float dx = fmaxf(fmaxf(bx0 - pj.x, pj.x - bx1), 0.f);
             const float dy = fmaxf(fmaxf(by0 - pj.y, pj.y - by1), 0.f);
             const float dz = fmaxf(fmaxf(bz0 - pj.z, pj.z - bz1), 0.f);
-            take = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= Ck2;
+            float lim2 = Ck2;
+            if (P::USES_HJ) {
+              // r < max(h_i, h_j): a j reaches the chunk only through its own h
+              const float cj = fmaxf(hmx, a.h[jidx]) + a.delta;
+              lim2 = cj * cj;
+            }
+            take = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= lim2;
           }
           const unsigned mt = __ballot_sync(FULL, take);
           const int nt = __popc(mt);
@@ -660,6 +702,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       }
       __syncwarp();
     }
+    }
   }
 }
 
@@ -667,7 +710,8 @@ template <class P, bool COUNT>
 int launch(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
   const int warps = c->prm.warps_per_cta;
   a.cap = c->sweep_cap;
-  size_t smem = (size_t)warps * (a.cap * P::JW + 32) * sizeof(float4);
+  a.bmax = c->prm.block_max;
+  size_t smem = (size_t)warps * (a.cap * P::JW + 32 + a.bmax / 4) * sizeof(float4);
   auto kern = k_sweep<P, COUNT>;
   if (smem > 48 * 1024)
     SPH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -768,6 +812,7 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   a.vel4 = c->vel4.as<float4>();
   a.fdat = c->fdat.as<float4>();
   a.blk_active = only_active ? c->blk_active.as<int>() : nullptr;
+  a.pflag = only_active ? c->h_flag.as<int>() : nullptr;
   a.queue = c->queue.as<int>();
   a.status = c->status.as<int>();
   double emax = 0;

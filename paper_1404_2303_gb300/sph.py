@@ -187,6 +187,7 @@ class SPH:
         d["sweep_launches"] = list(st.sweep_launches)
         d["sweep_units"] = list(st.sweep_units)
         d["sweep_candidates"] = list(st.sweep_candidates)
+        d["newton_active"] = list(st.newton_active)
         return d
 
     def profile(self, enable=True):

@@ -1,0 +1,95 @@
+"""GPU parity at the full sizes of the benchmark workloads, in the launch
+configuration bench.py times: the oracle recomputes a random sample of
+particles from scratch (its own h solve for them and for every particle
+their force sums reach) and the GPU values at those particles must agree
+within the parity tolerances.  The differentiable 64^3 configuration is
+checked in full against the oracle gradient."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sph_oracle as O
+import synth.configs as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _sph(**kw):
+    from paper_1404_2303_gb300 import SPH
+    return SPH(**kw)
+
+
+def _check_sample(x, m, u, v, h, rho, acc, sample, seed):
+    ref = O.evaluate_sample(x, m, u, sample, v=v)
+    assert np.max(np.abs(h[sample] - ref["h"]) / ref["h"]) <= 1e-5
+    assert np.max(np.abs(rho[sample] - ref["rho"]) / ref["rho"]) <= 1e-5
+    rms = np.sqrt(np.mean(np.sum(ref["a"] ** 2, axis=1)))
+    assert np.max(np.linalg.norm(acc[sample] - ref["a"], axis=1)) / rms <= 1e-4
+
+
+def _run(d, batched=False):
+    s = _sph()
+    if batched:
+        s.build_batch(_t(d["x"]), d["offsets"], d["boxes"])
+    else:
+        s.build(_t(d["x"]))
+    den = s.density(_t(d["m"]))
+    acc, _, _ = s.force(_t(d["u"]), _t(d["v"]))
+    torch.cuda.synchronize()
+    return (den["h"].cpu().numpy().astype(np.float64), den["rho"].cpu().numpy().astype(np.float64),
+            acc.cpu().numpy().astype(np.float64), s.stats())
+
+
+@pytest.mark.parametrize("name", ["multires128", "lognormal256"])
+def test_full_size_sampled_parity(name):
+    d = C.multires(128, seed=2) if name == "multires128" else C.lognormal(256, seed=5, sigma=4.0)
+    h, rho, acc, st = _run(d)
+    rng = np.random.default_rng(11)
+    n = d["x"].shape[0]
+    sample = np.sort(rng.choice(n, 200, replace=False))
+    # include the particles with the smallest and the largest h
+    sample = np.unique(np.concatenate([sample, [np.argmin(h), np.argmax(h)]]))
+    _check_sample(d["x"], d["m"], d["u"], d["v"], h, rho, acc, sample, 11)
+    if name == "lognormal256":
+        assert h.max() / h.min() > 300  # the clustered set spans a wide h range
+
+
+def test_batch64_sampled_parity():
+    d = C.concat_boxes(C.batch_boxes(64, seed=3))
+    h, rho, acc, st = _run(d, batched=True)
+    assert st["nbox"] == 64
+    off = d["offsets"]
+    rng = np.random.default_rng(12)
+    for b in (0, 17, 63):
+        sl = slice(off[b], off[b + 1])
+        nb = off[b + 1] - off[b]
+        sample = np.sort(rng.choice(nb, 60, replace=False))
+        _check_sample(d["x"][sl], d["m"][sl], d["u"][sl], d["v"][sl], h[sl], rho[sl], acc[sl],
+                      sample, b)
+
+
+def test_sinusoid64_gradient_full():
+    d = C.sinusoid(64, seed=4)
+    s = _sph()
+    s.build(_t(d["x"]))
+    den = s.density(_t(d["m"]))
+    acc, _, _ = s.force(_t(d["u"]))
+    g_pos, g_m, g_u = s.adjoint(2.0 * (den["rho"] - 1.0), 2.0 * acc, None)
+    torch.cuda.synchronize()
+    ref = O.evaluate(d["x"], d["m"], d["u"], h_guess=2.25 / 64)
+    gref = O.gradient(ref, d["x"], d["m"], d["u"], None, 2.0 * (ref["rho"] - 1.0), 2.0 * ref["a"])
+    for got, want in ((g_pos, gref["g_x"]), (g_m, gref["g_m"]), (g_u, gref["g_u"])):
+        gg = got.cpu().numpy().astype(np.float64).reshape(want.shape)
+        assert np.linalg.norm(gg - want) / np.linalg.norm(want) <= 1e-3
+        rms = np.sqrt(np.mean(want ** 2))
+        assert np.quantile(np.abs(gg - want).ravel() / (rms + np.abs(want).ravel()), 0.999) <= 1e-3
