@@ -85,6 +85,9 @@ typedef struct sph_params {
                            rebuilds); the solve starts from the estimate itself; 1.5 */
   int32_t sweep_cap;    /* sweep kernels: j-particles a warp buffers in shared memory between
                            compute passes (multiple of 32, 32..1024); 128 */
+  int32_t use_graph;    /* 1: each h-iteration round runs as one CUDA graph with a device-side
+                           while loop (no host round trip per iteration); 0: host loop.
+                           Profiling (sph_profile) always uses the host loop; 1 */
 } sph_params;
 
 /* Statistics of the last build and sweeps (host copy). */
@@ -231,6 +234,14 @@ int sph_pairs_dump(sph_ctx* ctx, int32_t phase, int64_t cap, int32_t* pi, int32_
  * either call resets the accumulated times.  sph_get_stats synchronises on
  * the recorded events and reports per-phase totals. */
 int sph_profile(sph_ctx* ctx, int32_t enable);
+
+/* Change the sweep launch shape of a built context (the decomposition is
+ * kept): warps per CTA (1..8), shared-memory j buffer per warp (multiple of
+ * 32, 32..1024) and resident CTAs per SM for the persistent grid (0 =
+ * occupancy).  Results do not depend on these; speed does (the autotuner
+ * in the Python package searches them). */
+int sph_set_sweep_config(sph_ctx* ctx, int32_t warps_per_cta, int32_t sweep_cap,
+                         int32_t ctas_per_sm);
 
 /* Copy the statistics of the last calls into *out. */
 int sph_get_stats(sph_ctx* ctx, sph_stats* out);

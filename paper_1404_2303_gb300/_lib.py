@@ -27,6 +27,7 @@ class SphParams(C.Structure):
         ("max_rebuild", C.c_int32), ("kahan", C.c_int32), ("morton_bits", C.c_int32),
         ("h_tol", C.c_float), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
         ("h_est_mode", C.c_int32), ("h_est_factor", C.c_float), ("sweep_cap", C.c_int32),
+        ("use_graph", C.c_int32),
     ]
 
 
@@ -64,6 +65,7 @@ SIGNATURES = {
     "sph_pairs_dump": (C.c_int, [P, C.c_int32, C.c_int64, P, P, C.POINTER(C.c_int64), P]),
     "sph_get_stats": (C.c_int, [P, C.POINTER(SphStats)]),
     "sph_profile": (C.c_int, [P, C.c_int32]),
+    "sph_set_sweep_config": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
     "sph_launch_count": (C.c_int64, []),
     "sph_density_small_noalloc": (C.c_int, [C.c_int32, P, C.c_double, P, P, C.c_float, C.c_int32,
                                             P, P, C.POINTER(C.c_int32), P]),

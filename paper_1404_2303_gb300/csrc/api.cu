@@ -133,6 +133,16 @@ __global__ void k_hsolve_update(long long n, float* h, const float* hlim, const 
   atomicAdd(nactive, 1);
 }
 
+// body end of the device-side h iteration: record this iteration's active
+// count and continue while particles are still iterating (max_newton cap)
+__global__ void k_loop_ctl(const int* nact, int* iter, int* hist, int maxit,
+                           cudaGraphConditionalHandle hnd) {
+  const int it = *iter, na = *nact;
+  if (it < 32) hist[it] = na;
+  *iter = it + 1;
+  cudaGraphSetConditional(hnd, (na > 0 && it + 1 < maxit) ? 1u : 0u);
+}
+
 __global__ void k_block_active(int nblock, const int* b_first, const int* b_count, const int* flag,
                                int* act) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -257,6 +267,72 @@ static int count_total(sph_ctx* c, unsigned long long* out, cudaStream_t s) {
   return SPH_OK;
 }
 
+static void graph_release(sph_ctx* c) {
+  if (c->g_exec) cudaGraphExecDestroy(c->g_exec);
+  if (c->g_graph) cudaGraphDestroy(c->g_graph);
+  c->g_exec = nullptr;
+  c->g_graph = nullptr;
+}
+
+// One solve round as a CUDA graph: a WHILE conditional node whose body
+// (active blocks, density sweep over them, h update, loop control) runs
+// on the device until no particle is iterating or max_newton is reached;
+// the host reads the counters once at the end.  The graph bakes in the
+// decomposition's buffers, so it is captured again after every build.
+static int solve_round_graph(sph_ctx* c, cudaStream_t s, int* host, int* iters) {
+  const long long n = c->n;
+  int* ctl = c->solve_ctl.as<int>();  // [0] active [1] at limit [2] iteration [3..34] history
+  if (!c->g_exec || c->g_gen != c->build_gen) {
+    graph_release(c);
+    cudaGraph_t g = nullptr;
+    SPH_CUDA(cudaGraphCreate(&g, 0));
+    c->g_graph = g;
+    cudaGraphConditionalHandle hnd;
+    SPH_CUDA(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    SPH_CUDA(cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs = c->cap_stream;
+    const long long before = launch_count();
+    SPH_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int r = SPH_OK;
+    { k_block_active<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, cs>>>(
+        c->nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->h_flag.as<int>(),
+        c->blk_active.as<int>()); note_launch(); }
+    if (r == SPH_OK) r = run_sweep(c, PH_DENSITY, 1, 0, cs);
+    if (r == SPH_OK && cudaMemsetAsync(ctl, 0, sizeof(int), cs) != cudaSuccess) r = SPH_ERR_CUDA;
+    { k_hsolve_update<<<div_up(n, TPB), TPB, 0, cs>>>(
+        n, c->h.as<float>(), c->hlim.as<float>(), c->nngb.as<float>(), c->dnngb.as<float>(),
+        c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_dx.as<float>(), c->h_flag.as<int>(),
+        c->prm.n_ngb, c->prm.h_tol, ctl, ctl + 1); note_launch(); }
+    { k_loop_ctl<<<1, 1, 0, cs>>>(ctl, ctl + 2, ctl + 3, c->prm.max_newton, hnd); note_launch(); }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &captured);
+    c->g_body_kernels = launch_count() - before;  // captured, not executed
+    note_launch_n(-c->g_body_kernels);
+    if (r != SPH_OK) return r;
+    SPH_CUDA(e);
+    SPH_CUDA(cudaGraphInstantiate(&c->g_exec, g, 0));
+    c->g_gen = c->build_gen;
+  }
+  SPH_CUDA(cudaMemsetAsync(ctl + 1, 0, 34 * sizeof(int), s));
+  SPH_CUDA(cudaGraphLaunch(c->g_exec, s));
+  int h_ctl[35];
+  SPH_CUDA(cudaMemcpyAsync(h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
+  host[0] = h_ctl[0];
+  host[1] = h_ctl[1];
+  *iters = h_ctl[2];
+  note_launch_n(c->g_body_kernels * h_ctl[2]);  // body kernels the graph ran
+  for (int k = 0; k < 32; ++k) c->stats.newton_active[k] = h_ctl[3 + k];
+  return SPH_OK;
+}
+
 extern "C" {
 
 void sph_default_params(sph_params* p) {
@@ -277,6 +353,7 @@ void sph_default_params(sph_params* p) {
   p->h_est_mode = 1;
   p->h_est_factor = 1.5f;
   p->sweep_cap = 128;
+  p->use_graph = 1;
 }
 
 int sph_create(const sph_params* p, sph_ctx** out) {
@@ -302,6 +379,12 @@ int sph_create(const sph_params* p, sph_ctx** out) {
   }
   cudaMemset(c->status.p, 0, 64);
   cudaMemset(c->counters.p, 0, 64);
+  if ((r = dbuf_ensure(c->solve_ctl, 64 * sizeof(int))) != SPH_OK ||
+      cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      (r = set_dir_table(c)) != SPH_OK) {
+    sph_destroy(c);
+    return r != SPH_OK ? r : SPH_ERR_CUDA;
+  }
   *out = c;
   return SPH_OK;
 }
@@ -319,7 +402,7 @@ void sph_destroy(sph_ctx* c) {
                  &c->dnngb, &c->d2rho, &c->omega, &c->Avec, &c->fdat, &c->vel4, &c->u_s, &c->acc4,
                  &c->cnt_i, &c->h_lo, &c->h_hi, &c->h_dx, &c->h_flag, &c->blk_active, &c->adj4, &c->adj4b, &c->g_A,
                  &c->g_rho_s, &c->g_drho_s, &c->g_h_s, &c->g_u_s, &c->g_x4,
-                 &c->prof_units, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
+                 &c->prof_units, &c->solve_ctl, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
                  &c->tmp_b, &c->tmp_c};
   for (DBuf* b : all) dbuf_free(*b);
   for (auto& e : c->ev_pending) {
@@ -327,6 +410,8 @@ void sph_destroy(sph_ctx* c) {
     cudaEventDestroy(e.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  graph_release(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 
@@ -432,6 +517,9 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
     // nlim accumulates over the whole solve: a particle flagged at its cell
     // limit in any iteration leaves the active set and must trigger the rebuild
     SPH_CUDA(cudaMemsetAsync(nlim, 0, sizeof(int), s));
+    if (c->prm.use_graph && !c->profile) {
+      SPH_TRY(solve_round_graph(c, s, host, &it));
+    } else {
     for (; it < c->prm.max_newton; ++it) {
       { k_block_active<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, s>>>(
           c->nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->h_flag.as<int>(),
@@ -451,6 +539,7 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
         ++it;
         break;
       }
+    }
     }
     total_iters += it;
     c->stats.unconverged = host[0];
@@ -549,6 +638,19 @@ int sph_pairs_dump(sph_ctx* c, int32_t phase, int64_t cap, int32_t* pi, int32_t*
   *n_out = (int64_t)nn;
   if ((long long)nn > cap) return SPH_ERR_CAPACITY;
   return read_status(c, s);
+}
+
+int sph_set_sweep_config(sph_ctx* c, int32_t warps_per_cta, int32_t sweep_cap,
+                         int32_t ctas_per_sm) {
+  if (!c || warps_per_cta < 1 || warps_per_cta > 8 || sweep_cap < 32 || sweep_cap > 1024 ||
+      (sweep_cap % 32) != 0 || ctas_per_sm < 0)
+    return SPH_ERR_INVALID_ARG;
+  c->prm.warps_per_cta = warps_per_cta;
+  c->prm.sweep_cap = sweep_cap;
+  c->sweep_cap = sweep_cap;
+  c->prm.ctas_per_sm = ctas_per_sm;
+  ++c->build_gen;  // captured graphs hold the old launch shape
+  return SPH_OK;
 }
 
 int sph_profile(sph_ctx* c, int32_t enable) {

@@ -1274,6 +1274,7 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
 
 int build_from_guess(sph_ctx* c, cudaStream_t s) {
   const long long n = c->n;
+  ++c->build_gen;  // device-side graphs hold this decomposition's buffers
   SPH_TRY(choose_top_levels(c, s));
   SPH_TRY(build_tree(c, 0, s));
   { k_relpos<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), c->xs.as<double>(),

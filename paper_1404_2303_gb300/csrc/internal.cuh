@@ -155,6 +155,12 @@ struct sph_ctx {
   int sweep_grid = 0;
   int sweep_cap = 128;  // buffered j-particles per warp in the sweeps
   bool dir_table_set = false;
+  // device-side h iteration graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t g_graph = nullptr;
+  cudaGraphExec_t g_exec = nullptr;
+  long long build_gen = 0, g_gen = -1, g_body_kernels = 0;
+  DBuf solve_ctl;
   int sweep_threads = 0;
   // profiling: (phase, start, stop) events recorded around sweep launches
   bool profile = false;
@@ -179,6 +185,7 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
 // (Morton order and positions unchanged)
 int build_from_guess(sph_ctx* c, cudaStream_t s);
 int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t s);
+int set_dir_table(sph_ctx* c);  // the 13 sort directions into constant memory (once)
 int compute_node_hmax(sph_ctx* c, cudaStream_t s);
 
 // sweep phases
@@ -196,4 +203,5 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // running count of kernel launches issued by this library (all contexts)
 void note_launch();
+void note_launch_n(long long k);  // adjust by k (graph-executed launches)
 long long launch_count();

@@ -783,16 +783,20 @@ int prof_resolve(sph_ctx* c) {
   return SPH_OK;
 }
 
+int set_dir_table(sph_ctx* c) {
+  if (c->dir_table_set) return SPH_OK;
+  float t[SPH_NDIR][3];
+  for (int d = 0; d < SPH_NDIR; ++d) dir_unit(d, t[d][0], t[d][1], t[d][2]);
+  SPH_CUDA(cudaMemcpyToSymbol(c_dir, t, sizeof(t)));
+  c->dir_table_set = true;
+  return SPH_OK;
+}
+
 int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t s) {
   if (c->nblock == 0) return SPH_OK;
   c->cur_phase = phase;
   if (c->profile && phase < PH_DUMP_DENSITY) counting = 1;
-  if (!c->dir_table_set) {
-    float t[SPH_NDIR][3];
-    for (int d = 0; d < SPH_NDIR; ++d) dir_unit(d, t[d][0], t[d][1], t[d][2]);
-    SPH_CUDA(cudaMemcpyToSymbolAsync(c_dir, t, sizeof(t), 0, cudaMemcpyHostToDevice, s));
-    c->dir_table_set = true;
-  }
+  SPH_TRY(set_dir_table(c));
   SweepArgs a{};
   a.nblock = c->nblock;
   a.order = c->b_order.as<int>();

@@ -190,6 +190,13 @@ class SPH:
         d["newton_active"] = list(st.newton_active)
         return d
 
+    def set_sweep_config(self, warps_per_cta, sweep_cap, ctas_per_sm=0):
+        check(self.lib.sph_set_sweep_config(self.h, int(warps_per_cta), int(sweep_cap),
+                                            int(ctas_per_sm)), "sph_set_sweep_config")
+        self.params.warps_per_cta = int(warps_per_cta)
+        self.params.sweep_cap = int(sweep_cap)
+        self.params.ctas_per_sm = int(ctas_per_sm)
+
     def profile(self, enable=True):
         check(self.lib.sph_profile(self.h, 1 if enable else 0), "sph_profile")
 

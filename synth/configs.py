@@ -208,7 +208,7 @@ def zeldovich(n_side: int = 256, seed: int = 5, amp: float = 8.0) -> dict:
     disp = []
     for K in (KX, KY, KZ):
         psi_k = 1j * K * delta_k / k2
-        disp.append(np.fft.irfftn(psi_k, s=(n, n, n)).ravel())
+        disp.append(np.fft.irfftn(psi_k, s=(n, n, n), axes=(0, 1, 2)).ravel())
     disp = np.stack(disp, axis=1)
     disp *= amp * a / np.sqrt(np.mean(np.sum(disp ** 2, axis=1)))
     g = (np.arange(n) + 0.5) * a
@@ -228,7 +228,7 @@ def _grf(n: int, rng: np.random.Generator, slope: float = -2.0) -> np.ndarray:
     wk = np.fft.rfftn(rng.standard_normal((n, n, n)))
     wk *= k2 ** (slope / 4.0)
     wk[0, 0, 0] = 0.0
-    g = np.fft.irfftn(wk, s=(n, n, n))
+    g = np.fft.irfftn(wk, s=(n, n, n), axes=(0, 1, 2))
     return g / g.std()
 
 

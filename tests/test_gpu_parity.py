@@ -158,3 +158,41 @@ def test_errors_are_reported():
     with pytest.raises(SphError) as e:
         s2.density(_t(d["m"]))  # nothing built
     assert e.value.code == -6
+
+
+def test_graph_loop_matches_host_loop():
+    """The device-side graph iteration and the host loop run the same kernels
+    in the same order: identical h and densities, same iteration count."""
+    d = C.random_box(20000, 7, "clumped")
+    out = {}
+    for g in (0, 1):
+        s = _sph(use_graph=g)
+        s.build(_t(d["x"]))
+        den = s.density(_t(d["m"]))
+        out[g] = (den["h"].cpu().numpy(), den["rho"].cpu().numpy(), den["iters"],
+                  s.stats()["newton_active"])
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+    assert out[0][3] == out[1][3]
+
+
+def test_autotuner_shapes_do_not_change_results():
+    """Launch shapes change the grouping of the compensated partial sums only:
+    at a fixed h the sums agree to FP32 rounding."""
+    from paper_1404_2303_gb300.autotune import tune
+    d = C.multires(32, seed=2)
+    pos, m, u = _t(d["x"]), _t(d["m"]), _t(d["u"])
+    shape, timings = tune(pos, m, u, use_cache=False, repeats=1)
+    assert len(timings) >= 4 and set(shape) == {"warps_per_cta", "sweep_cap", "ctas_per_sm"}
+    s = _sph()
+    s.build(pos)
+    h = s.density(m)["h"]
+    ref = s.density_fixed_h(m, h)["rho"].cpu().numpy().astype(np.float64)
+    acc_ref = s.force(u)[0].cpu().numpy().astype(np.float64)
+    for cand in timings:
+        s.set_sweep_config(cand["warps_per_cta"], cand["sweep_cap"], cand["ctas_per_sm"])
+        rho = s.density_fixed_h(m, h)["rho"].cpu().numpy().astype(np.float64)
+        acc = s.force(u)[0].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(rho - ref) / ref) <= 1e-6
+        assert _rms_err(acc, acc_ref) <= 1e-5
