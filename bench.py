@@ -62,6 +62,25 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def profiled_traffic(phase_name):
+    """DRAM bytes per launch of a sweep phase from the committed ncu summary,
+    or None when the sweep kernel source changed since that capture."""
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_1404_2303_gb300", "csrc", "sweep.cu")
+    summ = os.path.join(ROOT, "profiles", "sweep_kernels_multires128.md")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        text = open(summ).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256: ([0-9a-f]{64})", text)
+    t = re.search(r"traffic_bytes_per_launch\[" + re.escape(phase_name) + r"\]: ([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != sha:
+        return None
+    return float(t.group(1))
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -356,7 +375,7 @@ def main():
         achieved = k["units_per_launch"] * INSTR[dom] / (k["ms_per_launch"] / 1e3)
         roof = {"kernel": f"k_sweep<{dname}>", "bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak_alu / 1e12, "unit": "T FP32-instr/s",
-                "frac": achieved / peak_alu, "traffic": None,
+                "frac": achieved / peak_alu, "traffic": profiled_traffic(dname),
                 "peak_source": f"{SMS} SMs x {LANES} FP32 lanes x {sm_max:.0f} MHz "
                                f"(sm_max_mhz of {pk_kind} peaks)",
                 "instr_per_unit": INSTR[dom]}

@@ -690,6 +690,11 @@ __device__ __forceinline__ bool mergeable(int node, const int* need, const int* 
   return need[node] != 0 && count[node] > 0 && !(child0[node] < 0 && nblk[node] <= 1);
 }
 
+__global__ void k_gather_i64(int n, const int* idx, const long long* in, long long* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[idx[i]];
+}
+
 __global__ void k_merge_count(int g0, int g1, const int* need, const int* child0, const int* nblk,
                               const int* count, long long* elems) {
   int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -699,12 +704,13 @@ __global__ void k_merge_count(int g0, int g1, const int* need, const int* child0
                          : 0;
 }
 
-__global__ void k_merge_flat(int g0, int ng, const long long* off, long long total, const int* need,
-                             const int* child0, const int* count, const int* nblk, const int* blk0,
-                             const int* b_first, const int* b_count, const long long* sbase,
-                             float* s_key, int* s_idx) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
+__global__ void k_merge_flat(int g0, int ng, const long long* off, long long base, long long total,
+                             const int* need, const int* child0, const int* count, const int* nblk,
+                             const int* blk0, const int* b_first, const int* b_count,
+                             const long long* sbase, float* s_key, int* s_idx) {
+  for (long long el = blockIdx.x * (long long)blockDim.x + threadIdx.x; el < total;
+       el += (long long)gridDim.x * blockDim.x) {
+    const long long e = base + el;
     // node: last index with off[i] <= e
     int lo = 0, hi = ng;
     while (hi - lo > 1) {
@@ -1141,26 +1147,40 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
                                                        c->s_key.as<float>(), c->s_idx.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
   }
-  for (int g = (int)c->gen_start.size() - 2; g >= 0; --g) {
-    int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
-    int ng = g1 - g0;
-    if (ng <= 0) continue;
-    SPH_TRY(dbuf_ensure(sz, sizeof(long long) * (size_t)(2 * ng + 2)));
+  {
+    // merge elements of every cell in one scan (cells are numbered by
+    // generation), one host read of the per-generation offsets, then the
+    // generations from the deepest up (children before parents)
+    const int ng_all = ncell;
+    SPH_TRY(dbuf_ensure(sz, sizeof(long long) * (size_t)(2 * ng_all + 2 + 2 * c->gen_start.size())));
     long long* el = sz.as<long long>();
-    long long* eo = el + (ng + 1);
-    { k_merge_count<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, need, c->n_child0.as<int>(), nblk,
-                                                   c->n_count.as<int>(), el); note_launch(); }
+    long long* eo = el + (ng_all + 1);
+    long long* ego = eo + (ng_all + 1);
+    { k_merge_count<<<div_up(ng_all, TPB), TPB, 0, s>>>(0, ng_all, need, c->n_child0.as<int>(), nblk,
+                                                       c->n_count.as<int>(), el); note_launch(); }
     SPH_CUDA(cudaGetLastError());
-    SPH_TRY(scan_exclusive_i64(el, eo, ng, eo + ng, c->scan_tmp, s));
-    long long total = 0;
-    SPH_TRY(d2h(&total, eo + ng, s));
-    if (total == 0) continue;
-    int grid = (int)std::min<long long>(div_up(total, TPB), 152ll * 64);
-    { k_merge_flat<<<grid, TPB, 0, s>>>(g0, ng, eo, total, need, c->n_child0.as<int>(),
-                                       c->n_count.as<int>(), nblk, blk0, c->b_first.as<int>(),
-                                       c->b_count.as<int>(), c->n_sbase.as<long long>(),
-                                       c->s_key.as<float>(), c->s_idx.as<int>()); note_launch(); }
+    SPH_TRY(scan_exclusive_i64(el, eo, ng_all, eo + ng_all, c->scan_tmp, s));
+    const int ngen = (int)c->gen_start.size();
+    SPH_TRY(dbuf_ensure(c->tmp_a, sizeof(int) * (size_t)ngen + 64));
+    SPH_CUDA(cudaMemcpyAsync(c->tmp_a.p, c->gen_start.data(), sizeof(int) * ngen,
+                             cudaMemcpyHostToDevice, s));
+    { k_gather_i64<<<div_up(ngen, TPB), TPB, 0, s>>>(ngen, c->tmp_a.as<int>(), eo, ego); note_launch(); }
     SPH_CUDA(cudaGetLastError());
+    std::vector<long long> goff(ngen);
+    SPH_CUDA(cudaMemcpyAsync(goff.data(), ego, sizeof(long long) * ngen, cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+    for (int g = ngen - 2; g >= 0; --g) {
+      const int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
+      const long long total = goff[g + 1] - goff[g];
+      if (g1 <= g0 || total <= 0) continue;
+      int grid = (int)std::min<long long>(div_up(total, TPB), 152ll * 64);
+      { k_merge_flat<<<grid, TPB, 0, s>>>(g0, g1 - g0, eo + g0, goff[g], total, need,
+                                         c->n_child0.as<int>(), c->n_count.as<int>(), nblk, blk0,
+                                         c->b_first.as<int>(), c->b_count.as<int>(),
+                                         c->n_sbase.as<long long>(), c->s_key.as<float>(),
+                                         c->s_idx.as<int>()); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+    }
   }
   dbuf_free(sz);
 
