@@ -88,6 +88,17 @@ typedef struct sph_params {
   int32_t use_graph;    /* 1: each h-iteration round runs as one CUDA graph with a device-side
                            while loop (no host round trip per iteration); 0: host loop.
                            Profiling (sph_profile) always uses the host loop; 1 */
+  int32_t sweep_lists;  /* sweep kernels, bit k for phase k (0 density, 1 d2rho/dh2, 2 force,
+                           3 force adjoint, 4 density adjoint): each lane first tests every
+                           buffered candidate with the phase's exact FP32 predicate and keeps
+                           a list of the accepted ones, then evaluates only those (otherwise
+                           every lane evaluates every candidate); needs sweep_cap <= 256; 0x08 */
+  int32_t pair_list_cap;/* force pair lists: the force sweep records, per particle, every j with
+                           r < max(h_i, h_j) (up to this many; 0 disables), and the phases over
+                           that pair set afterwards (d2rho/dh2, force adjoint, density adjoint)
+                           read the lists instead of sweeping; a particle with more pairs is
+                           swept.  Costs 4 * n * pair_list_cap bytes of device memory; needs
+                           sweep_cap <= 256 and n < 2^27; 256 */
 } sph_params;
 
 /* Statistics of the last build and sweeps (host copy). */

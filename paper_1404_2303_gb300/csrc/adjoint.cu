@@ -46,13 +46,14 @@ __global__ void k_dens_adj_prep(long long n, const float* h, const float* drho, 
                                 const float* g_h, float4* adj4, float4* adj4b) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  float hi = 1.f / h[s];
+  const float hv = h[s];
+  float hi = 1.f / hv;
   float hi2 = hi * hi, hi3 = hi2 * hi, hi4 = hi2 * hi2;
   float gr = g_rho[s], grp = g_drho[s];
   float ghtot = g_h[s] + gr * drho[s] + grp * d2rho[s];
   float lam = ghtot / dnngb[s];
   adj4[s] = make_float4(hi, 2.f * SIGMA * hi3 * gr, 6.f * SIGMA * hi4 * grp, 6.f * SIGMA * hi4 * gr);
-  adj4b[s] = make_float4(SIGMA * hi4 * hi * grp, 64.f * lam * hi, 0.f, 0.f);
+  adj4b[s] = make_float4(SIGMA * hi4 * hi * grp, 64.f * lam * hi, __fmul_rn(hv, hv), 0.f);
 }
 
 __global__ void k_gather_f(long long n, const int* perm, const float* in, float* out, int add) {

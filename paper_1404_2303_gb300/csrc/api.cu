@@ -354,6 +354,8 @@ void sph_default_params(sph_params* p) {
   p->h_est_factor = 1.5f;
   p->sweep_cap = 128;
   p->use_graph = 1;
+  p->sweep_lists = 0x08;
+  p->pair_list_cap = 256;
 }
 
 int sph_create(const sph_params* p, sph_ctx** out) {
@@ -365,7 +367,8 @@ int sph_create(const sph_params* p, sph_ctx** out) {
       q.block_max < 32 || q.block_max > 256 || q.max_newton < 1 || q.max_rebuild < 0 ||
       q.morton_bits < 8 || q.morton_bits > 20 || !(q.h_tol > 0.f) || q.warps_per_cta < 1 ||
       q.warps_per_cta > 8 || q.ctas_per_sm < 0 || q.h_est_mode < 0 || q.h_est_mode > 1 ||
-      !(q.h_est_factor > 0.f) || q.sweep_cap < 32 || q.sweep_cap > 1024 || (q.sweep_cap % 32) != 0)
+      !(q.h_est_factor > 0.f) || q.sweep_cap < 32 || q.sweep_cap > 1024 || (q.sweep_cap % 32) != 0 ||
+      q.sweep_lists < 0 || q.sweep_lists > 0x1f || q.pair_list_cap < 0 || q.pair_list_cap > 4096)
     return SPH_ERR_INVALID_ARG;
   sph_ctx* c = new sph_ctx();
   c->prm = q;
@@ -426,6 +429,7 @@ int sph_build_batch(sph_ctx* c, int32_t nbox, const int64_t* offsets, const doub
   if (n <= 0 || n >= (1ll << 31) / 16) return SPH_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   c->built = c->have_density = c->have_force = false;
+  c->fl_valid = false;
   c->have_d2 = 0;
   c->n = n;
   c->nbox = nbox;
@@ -483,6 +487,7 @@ int sph_density_fixed_h(sph_ctx* c, const float* m, const float* h, float* rho, 
   SPH_CUDA(cudaGetLastError());
   c->have_density = true;
   c->have_force = false;
+  c->fl_valid = false;
   c->have_d2 = 0;
   if (count) {
     { k_scatter_i<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->cnt_i.as<int>(), count); note_launch(); }
@@ -587,6 +592,7 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
   }
   c->have_density = true;
   c->have_force = false;
+  c->fl_valid = false;
   c->have_d2 = 0;
   return read_status(c, s);
 }

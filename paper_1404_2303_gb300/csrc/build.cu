@@ -174,7 +174,7 @@ __global__ void k_scale(long long n, float* v, float f) {
 }
 
 __global__ void k_relpos(long long n, const unsigned long long* keys, const double* xs,
-                         const double* Ls, const int* box_t, int K, float4* pos4) {
+                         const double* Ls, const int* box_t, int K, float4* pos4, float* p_et) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
   unsigned long long key = keys[s];
@@ -189,6 +189,7 @@ __global__ void k_relpos(long long n, const unsigned long long* keys, const doub
   v.z = (float)(xs[3 * s + 2] - iz * e);
   v.w = 0.f;
   pos4[s] = v;
+  p_et[s] = (float)e;
 }
 
 // ---------------------------------------------------------------- tasks
@@ -1259,6 +1260,7 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
   SPH_TRY(dbuf_ensure(c->hguess, 4 * (size_t)n));
   SPH_TRY(dbuf_ensure(c->h, 4 * (size_t)n));
   SPH_TRY(dbuf_ensure(c->pos4, 16 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->p_et, 4 * (size_t)n));
   { k_keys<<<div_up(n, TPB), TPB, 0, s>>>(pos, n, c->d_box_off.as<long long>(),
                                         c->d_box_L.as<double>(), c->nbox, K,
                                         c->keys.as<unsigned long long>(), c->perm.as<int>()); note_launch(); }
@@ -1299,7 +1301,7 @@ int build_from_guess(sph_ctx* c, cudaStream_t s) {
   SPH_TRY(build_tree(c, 0, s));
   { k_relpos<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), c->xs.as<double>(),
                                           c->d_box_L.as<double>(), c->d_box_t.as<int>(), c->kbits,
-                                          c->pos4.as<float4>()); note_launch(); }
+                                          c->pos4.as<float4>(), c->p_et.as<float>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   SPH_TRY(build_tasks(c, s));
   SPH_TRY(build_blocks_and_sorts(c, s));

@@ -94,6 +94,7 @@ struct sph_ctx {
   DBuf hguess;    // float build-time h
   DBuf hlim;      // float per-particle cell limit
   DBuf pnode;     // int leaf node of each particle
+  DBuf p_et;      // float top-cell edge of each particle's box
 
   // octree nodes
   int ncell = 0, ntop = 0, max_depth = 0;
@@ -141,6 +142,16 @@ struct sph_ctx {
   // adjoint state
   DBuf adj4, adj4b;  // adjoint per-particle j data (cell order)
   DBuf g_A, g_rho_s, g_drho_s, g_h_s, g_u_s, g_x4;
+  // force pair lists: per particle (cell order), the j of every pair
+  // r < max(h_i, h_j) with its top-cell image code, recorded by the force
+  // sweep; later phases over the same pair set read them instead of sweeping
+  DBuf fl_list;      // unsigned, groups of 32 particles x fl_K entries x 32 lanes
+  DBuf fl_cnt;       // int entries per particle, -1 when the list overflowed
+  DBuf fl_flag;      // int bit 0: list overflowed (swept instead)
+  DBuf fl_blk;       // int per block: holds an overflowed particle
+  DBuf fl_over;      // int number of overflowed particles
+  int fl_K = 0;
+  bool fl_valid = false;
 
   // misc
   DBuf status;       // int device status word + counters

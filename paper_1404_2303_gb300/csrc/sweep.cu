@@ -53,6 +53,15 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 
 __constant__ float c_dir[SPH_NDIR][3];
 
+// a pair-list entry: j (27 bits) and the top-cell image of j seen from i,
+// one of (-1, 0, 1)^3 (5 bits): the shift is that vector times the box's
+// top-cell edge, exactly the float shift of the pair task
+constexpr unsigned TAG_J = (1u << 27) - 1u;
+__device__ __forceinline__ int img_of(float s) { return s > 0.f ? 2 : (s < 0.f ? 0 : 1); }
+__device__ __forceinline__ unsigned make_tag(int j, float sx, float sy, float sz) {
+  return (unsigned)j | ((unsigned)(img_of(sx) * 9 + img_of(sy) * 3 + img_of(sz)) << 27);
+}
+
 struct SweepArgs {
   int nblock;
   int cap;  // buffered j-particles per warp between two compute passes
@@ -90,6 +99,16 @@ struct SweepArgs {
   float4* o5;
   int* ocnt;
   unsigned long long* units;  // profiling: accepted pairs of this launch
+  // force pair lists (written by the force sweep, read by k_listeval)
+  unsigned* fl_list;
+  int* fl_cnt;
+  int* fl_flag;
+  int* fl_blk;
+  int* fl_over;
+  int fl_K;
+  const float* p_et;
+  long long n;
+  const int* run_if;    // non-null: the launch does nothing when *run_if == 0
   // pair dump
   const int* perm;
   int* dump_i;
@@ -106,6 +125,7 @@ struct SweepArgs {
 struct PDensity {
   static constexpr int NACC = 4;
   static constexpr int JW = 1;
+  static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = false;
   struct I {
     float x, y, z, h, hinv, h2;
@@ -123,8 +143,15 @@ struct PDensity {
     i.h = 0.f; i.hinv = 0.f; i.h2 = 0.f;
   }
   __device__ static float cut_h(float h, float) { return h; }
-  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+  __device__ static void stage(const SweepArgs& a, int j, unsigned tag, float4 pj, float4* tile, int lane,
+                                int cap) {
     tile[lane] = pj;
+  }
+  // the directed-interaction predicate r < h_i in FP32
+  __device__ static bool test(const I& i, const float4* tile, int t, int cap) {
+    float4 p = tile[t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < i.h2;
   }
   template <bool COUNT>
   __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
@@ -159,13 +186,18 @@ struct PDensity {
 struct PDensityD2 {
   static constexpr int NACC = 1;
   static constexpr int JW = 1;
+  static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = false;
   using I = PDensity::I;
   __device__ static void load_i(const SweepArgs& a, int p, I& i) { PDensity::load_i(a, p, i); }
   __device__ static void null_i(I& i) { PDensity::null_i(i); }
   __device__ static float cut_h(float h, float) { return h; }
-  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
-    PDensity::stage(a, j, pj, tile, lane, cap);
+  __device__ static void stage(const SweepArgs& a, int j, unsigned tag, float4 pj, float4* tile, int lane,
+                                int cap) {
+    PDensity::stage(a, j, tag, pj, tile, lane, cap);
+  }
+  __device__ static bool test(const I& i, const float4* tile, int t, int cap) {
+    return PDensity::test(i, tile, t, cap);
   }
   template <bool COUNT>
   __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
@@ -197,6 +229,7 @@ struct PDensityD2 {
 struct PForce {
   static constexpr int NACC = 4;
   static constexpr int JW = 3;
+  static constexpr bool WRITES = true;  // records the pair lists
   static constexpr bool USES_HJ = true;
   struct I {
     float x, y, z, vx, vy, vz, h, hinv, h2, C;
@@ -220,11 +253,19 @@ struct PForce {
     i.p = -1;
   }
   __device__ static float cut_h(float h, float hj) { return fmaxf(h, hj); }
-  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+  __device__ static void stage(const SweepArgs& a, int j, unsigned tag, float4 pj, float4* tile, int lane,
+                                int cap) {
     tile[lane] = pj;
     tile[cap + lane] = a.vel4[j];
     float4 f = a.fdat[j];
-    tile[2 * cap + lane] = make_float4(f.x, f.y, f.z, __int_as_float(j));
+    tile[2 * cap + lane] = make_float4(f.x, f.y, f.z, __uint_as_float(tag));
+  }
+  // the force-pair predicate r < max(h_i, h_j) in FP32
+  __device__ static bool test(const I& i, const float4* tile, int t, int cap) {
+    float4 p = tile[t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    return r2 < fmaxf(i.h2, tile[2 * cap + t].y);
   }
   template <bool COUNT>
   __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
@@ -247,7 +288,7 @@ struct PForce {
     acc[2] = fmaf(coef, dz, acc[2]);
     float vd = fmaf(i.vz - v.z, dz, fmaf(i.vy - v.y, dy, (i.vx - v.x) * dx));
     acc[3] = fmaf(tm * rinv, vd, acc[3]);
-    if (COUNT) cnt += (r2 < fmaxf(i.h2, f.y) && __float_as_int(f.w) != i.p) ? 1 : 0;
+    if (COUNT) cnt += (r2 < fmaxf(i.h2, f.y) && (int)(__float_as_uint(f.w) & TAG_J) != i.p) ? 1 : 0;
   }
   __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
     float C = a.fdat[p].z;
@@ -271,28 +312,38 @@ struct PForce {
 struct PForceAdj {
   static constexpr int NACC = 6;  // gx, gy, gz, gm, gA, gh
   static constexpr int JW = 4;
+  static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = true;
   struct I {
-    float x, y, z, m, vx, vy, vz, h, hinv, A, ax, ay, az, ub;
+    float x, y, z, m, vx, vy, vz, h, hinv, h2, A, ax, ay, az, ub;
   };
   __device__ static void load_i(const SweepArgs& a, int p, I& i) {
-    float4 q = a.pos4[p], v = a.vel4[p], g = a.adj4[p];
+    float4 q = a.pos4[p], v = a.vel4[p], g = a.adj4[p], f = a.fdat[p];
     i.x = q.x; i.y = q.y; i.z = q.z; i.m = q.w;
     i.vx = v.x; i.vy = v.y; i.vz = v.z; i.hinv = v.w;
     i.h = a.h[p];
-    i.A = a.fdat[p].w;
+    i.h2 = f.y;
+    i.A = f.w;
     i.ax = g.x; i.ay = g.y; i.az = g.z; i.ub = g.w;
   }
   __device__ static void null_i(I& i) {
-    i.x = i.y = i.z = i.m = i.vx = i.vy = i.vz = i.h = i.hinv = i.A = 0.f;
+    i.x = i.y = i.z = i.m = i.vx = i.vy = i.vz = i.h = i.hinv = i.h2 = i.A = 0.f;
     i.ax = i.ay = i.az = i.ub = 0.f;
   }
   __device__ static float cut_h(float h, float hj) { return fmaxf(h, hj); }
-  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+  __device__ static void stage(const SweepArgs& a, int j, unsigned tag, float4 pj, float4* tile, int lane,
+                                int cap) {
     tile[lane] = pj;
     tile[cap + lane] = a.vel4[j];
     tile[2 * cap + lane] = a.adj4[j];
-    tile[3 * cap + lane] = make_float4(a.fdat[j].w, 0.f, 0.f, 0.f);
+    const float4 f = a.fdat[j];
+    tile[3 * cap + lane] = make_float4(f.w, f.y, 0.f, 0.f);
+  }
+  __device__ static bool test(const I& i, const float4* tile, int t, int cap) {
+    float4 p = tile[t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    return r2 < fmaxf(i.h2, tile[3 * cap + t].y);
   }
   template <bool COUNT>
   __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
@@ -357,25 +408,35 @@ struct PForceAdj {
 struct PDensityAdj {
   static constexpr int NACC = 4;  // gx, gy, gz, gm
   static constexpr int JW = 3;
+  static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = true;
   struct I {
-    float x, y, z, m, h, hinv, R, S, L;
+    float x, y, z, m, h, hinv, h2, R, S, L;
   };
   __device__ static void load_i(const SweepArgs& a, int p, I& i) {
     float4 q = a.pos4[p], u = a.adj4[p], w = a.adj4b[p];
     i.x = q.x; i.y = q.y; i.z = q.z; i.m = q.w;
     i.h = a.h[p];
     i.hinv = u.x;
+    i.h2 = w.z;
     i.R = u.w; i.S = w.x; i.L = w.y;
   }
   __device__ static void null_i(I& i) {
-    i.x = i.y = i.z = i.m = i.h = i.hinv = i.R = i.S = i.L = 0.f;
+    i.x = i.y = i.z = i.m = i.h = i.hinv = i.h2 = i.R = i.S = i.L = 0.f;
   }
   __device__ static float cut_h(float h, float hj) { return fmaxf(h, hj); }
-  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+  __device__ static void stage(const SweepArgs& a, int j, unsigned tag, float4 pj, float4* tile, int lane,
+                                int cap) {
     tile[lane] = pj;
     tile[cap + lane] = a.adj4[j];
     tile[2 * cap + lane] = a.adj4b[j];
+  }
+  // r < max(h_i, h_j); the self term (r = 0) is included
+  __device__ static bool test(const I& i, const float4* tile, int t, int cap) {
+    float4 p = tile[t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    return r2 < fmaxf(i.h2, tile[2 * cap + t].z);
   }
   template <bool COUNT>
   __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
@@ -413,6 +474,7 @@ template <int FORCE>
 struct PDump {
   static constexpr int NACC = 1;
   static constexpr int JW = 2;
+  static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = FORCE != 0;
   struct I {
     float x, y, z, h, h2;
@@ -435,11 +497,13 @@ struct PDump {
     i.a = nullptr;
   }
   __device__ static float cut_h(float h, float hj) { return FORCE ? fmaxf(h, hj) : h; }
-  __device__ static void stage(const SweepArgs& a, int j, float4 pj, float4* tile, int lane, int cap) {
+  __device__ static void stage(const SweepArgs& a, int j, unsigned tag, float4 pj, float4* tile, int lane,
+                                int cap) {
     float h = a.h[j];
     tile[lane] = pj;
     tile[cap + lane] = make_float4(__fmul_rn(h, h), __int_as_float(j), 0.f, 0.f);
   }
+  __device__ static bool test(const I&, const float4*, int, int) { return true; }
   template <bool COUNT>
   __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
     if (i.p < 0) return;
@@ -483,12 +547,49 @@ __device__ __forceinline__ void fold(float* acc, float* cmp, float* part, int ka
   }
 }
 
-template <class P, bool COUNT>
-__device__ __forceinline__ void compute_pass(const typename P::I& I, const float4* buf, int staged,
-                                             int cap, float* part, int& cnt) {
+// One compute pass over the buffered j-particles.  Without lists every lane
+// evaluates every buffered j (branch-free: the spline's clamps zero the
+// pairs beyond the support), so a warp pays the full interaction for each
+// candidate.  With lists each lane first applies the exact FP32 predicate
+// of its phase to every candidate and records the accepted slots in its own
+// column of a byte list (lane-private, so no synchronisation between the
+// two loops), then evaluates only those: the warp runs as long as its
+// longest list instead of the whole buffer.
+// A phase that records pair lists (WRITES) appends the tag of every
+// accepted pair to the lane's list column wl (entry k at wl[32 k]) while
+// wtot < wcap; wtot keeps counting past the capacity to flag the overflow.
+template <class P, bool COUNT, bool LIST>
+__device__ __forceinline__ void compute_pass(const typename P::I& I, bool vi, const float4* buf,
+                                             unsigned char* lst, int staged, int cap, float* part,
+                                             int& cnt, unsigned* wl, int& wtot, int wcap) {
   __syncwarp();
+  if (LIST) {
+    const int lane = threadIdx.x & 31;
+    int nl = 0;
+    if (vi) {
+#pragma unroll 4
+      for (int t = 0; t < staged; ++t) {
+        if (P::test(I, buf, t, cap)) {
+          lst[nl * 32 + lane] = (unsigned char)t;
+          ++nl;
+        }
+      }
+    }
+    const int nmax = __reduce_max_sync(FULL, nl);
+    for (int k = 0; k < nmax; ++k) {
+      if (k < nl) {
+        const int t = lst[k * 32 + lane];
+        P::template interact<COUNT>(I, buf, t, part, cnt, cap);
+        if (P::WRITES && wl) {
+          if (wtot < wcap) wl[(size_t)wtot * 32] = __float_as_uint(buf[2 * cap + t].w);
+          ++wtot;
+        }
+      }
+    }
+  } else {
 #pragma unroll 2
-  for (int t = 0; t < staged; ++t) P::template interact<COUNT>(I, buf, t, part, cnt, cap);
+    for (int t = 0; t < staged; ++t) P::template interact<COUNT>(I, buf, t, part, cnt, cap);
+  }
   __syncwarp();
 }
 
@@ -514,15 +615,24 @@ __device__ __forceinline__ int h_class(const SweepArgs& a, int p, float hmin) {
   return c > 15 ? 15 : c;
 }
 
-template <class P, bool COUNT>
+// shared memory of one warp, in float4: j buffer, chunk positions, the
+// block's particle order, and (list mode) the per-lane byte lists
+template <class P, bool LIST>
+__host__ __device__ __forceinline__ int warp_smem_f4(int cap, int bmax) {
+  return cap * P::JW + 32 + bmax / 4 + (LIST ? cap * 2 : 0);
+}
+
+template <class P, bool COUNT, bool LIST>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cap = a.cap;
-  float4* buf = smem + (size_t)warp * (cap * P::JW + 32 + a.bmax / 4);
+  float4* buf = smem + (size_t)warp * warp_smem_f4<P, LIST>(cap, a.bmax);
   float4* cpos = buf + cap * P::JW;  // the chunk's particles (x, y, z, h)
   int* ord = reinterpret_cast<int*>(cpos + 32);  // the block's particles grouped by h class
+  unsigned char* lst = reinterpret_cast<unsigned char*>(cpos + 32 + a.bmax / 4);
   const unsigned lt = (1u << lane) - 1u;
+  if (a.run_if && *a.run_if == 0) return;
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(a.queue, 1);
@@ -577,7 +687,10 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       float acc[P::NACC], cmp[P::NACC], part[P::NACC];
 #pragma unroll
       for (int k = 0; k < P::NACC; ++k) acc[k] = cmp[k] = part[k] = 0.f;
-      int cnt = 0, ncand = 0, staged = 0;
+      int cnt = 0, ncand = 0, staged = 0, wtot = 0;
+      unsigned* wl = (P::WRITES && LIST && a.fl_list && vi)
+                         ? a.fl_list + ((size_t)(pi >> 5) * a.fl_K) * 32 + (pi & 31)
+                         : nullptr;
       for (long long g = e0; g < e1; g += 32) {
         // ---- one lane per interaction task: window of the chunk in the
         // task cell's sorted list (the axial cutoff of the sorted sweep)
@@ -669,16 +782,18 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           const unsigned mt = __ballot_sync(FULL, take);
           const int nt = __popc(mt);
           if (staged + nt > cap) {
-            compute_pass<P, COUNT>(I, buf, staged, cap, part, cnt);
+            compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot, a.fl_K);
             if (COUNT && vi) ncand += staged;
             fold<P>(acc, cmp, part, a.kahan);
             staged = 0;
           }
-          if (take) P::stage(a, jidx, pj, buf, staged + __popc(mt & lt), cap);
+          if (take)
+            P::stage(a, jidx, P::WRITES ? make_tag(jidx, sx, sy, sz) : 0u, pj, buf,
+                     staged + __popc(mt & lt), cap);
           staged += nt;
         }
       }
-      compute_pass<P, COUNT>(I, buf, staged, cap, part, cnt);
+      compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot, a.fl_K);
       if (COUNT && vi) ncand += staged;
       fold<P>(acc, cmp, part, a.kahan);
       if (vi) {
@@ -687,6 +802,15 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         for (int k = 0; k < P::NACC; ++k) v[k] = acc[k] + cmp[k];
         P::finalize(a, pi, v);
         if (COUNT && a.ocnt) a.ocnt[pi] = cnt;
+        if (wl) {
+          const bool over = wtot > a.fl_K;
+          a.fl_cnt[pi] = over ? -1 : wtot;
+          a.fl_flag[pi] = over ? 1 : 0;
+          if (over) {
+            atomicAdd(a.fl_over, 1);
+            a.fl_blk[b] = 1;
+          }
+        }
       }
       if (COUNT && a.units) {
         int ct = vi ? cnt : 0;
@@ -706,13 +830,11 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   }
 }
 
-template <class P, bool COUNT>
-int launch(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
+template <class P, bool COUNT, bool LIST>
+int launch_shape(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
   const int warps = c->prm.warps_per_cta;
-  a.cap = c->sweep_cap;
-  a.bmax = c->prm.block_max;
-  size_t smem = (size_t)warps * (a.cap * P::JW + 32 + a.bmax / 4) * sizeof(float4);
-  auto kern = k_sweep<P, COUNT>;
+  size_t smem = (size_t)warps * warp_smem_f4<P, LIST>(a.cap, a.bmax) * sizeof(float4);
+  auto kern = k_sweep<P, COUNT, LIST>;
   if (smem > 48 * 1024)
     SPH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, nsm = 0, per_sm = c->prm.ctas_per_sm;
@@ -744,6 +866,140 @@ int launch(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
     c->ev_pending.push_back({c->cur_phase, e0, e1});
   }
   return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// a phase over the force pairs (or a subset of them) from the recorded pair
+// lists: one lane per particle, 32 consecutive particles per warp, each
+// lane walks its own list (coalesced: entry k of the warp's 32 particles is
+// one 128-byte row), stages its j in its own shared-memory slot and applies
+// the phase's predicate and interaction; particles whose list overflowed
+// are left to a masked sweep
+// ---------------------------------------------------------------------------
+constexpr int LE_WARPS = 8;
+
+template <class P, bool COUNT>
+__global__ void __launch_bounds__(LE_WARPS * 32) k_listeval(SweepArgs a) {
+  __shared__ float4 tiles[LE_WARPS][P::JW * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4* tile = tiles[warp];
+  const long long ngrp = (a.n + 31) >> 5;
+  for (long long g = (long long)blockIdx.x * LE_WARPS + warp; g < ngrp;
+       g += (long long)gridDim.x * LE_WARPS) {
+    const long long p = g * 32 + lane;
+    const int np = p < a.n ? a.fl_cnt[p] : -1;
+    const bool vi = np >= 0;
+    typename P::I I;
+    if (vi) P::load_i(a, (int)p, I); else P::null_i(I);
+    const float et = vi ? a.p_et[p] : 0.f;
+    float acc[P::NACC], cmp[P::NACC], part[P::NACC];
+#pragma unroll
+    for (int k = 0; k < P::NACC; ++k) acc[k] = cmp[k] = part[k] = 0.f;
+    int cnt = 0;
+    const int nmax = __reduce_max_sync(FULL, vi ? np : 0);
+    const unsigned* wl = a.fl_list + ((size_t)g * a.fl_K) * 32 + lane;
+    for (int k0 = 0; k0 < nmax; k0 += 32) {
+      const int k1 = min(nmax, k0 + 32);
+      for (int k = k0; k < k1; ++k) {
+        if (k < np) {
+          const unsigned e = wl[(size_t)k * 32];
+          const int j = (int)(e & TAG_J);
+          const int im = (int)(e >> 27);
+          const float4 q = a.pos4[j];
+          const float4 pj = make_float4(__fadd_rn(q.x, (float)(im / 9 - 1) * et),
+                                        __fadd_rn(q.y, (float)((im / 3) % 3 - 1) * et),
+                                        __fadd_rn(q.z, (float)(im % 3 - 1) * et), q.w);
+          P::stage(a, j, e, pj, tile, lane, 32);
+          if (P::test(I, tile, lane, 32)) P::template interact<COUNT>(I, tile, lane, part, cnt, 32);
+        }
+      }
+      fold<P>(acc, cmp, part, a.kahan);
+    }
+    if (vi) {
+      float v[P::NACC];
+#pragma unroll
+      for (int k = 0; k < P::NACC; ++k) v[k] = acc[k] + cmp[k];
+      P::finalize(a, (int)p, v);
+      if (COUNT && a.ocnt) a.ocnt[p] = cnt;
+    }
+    if (COUNT && a.units) {
+      int ct = vi ? cnt : 0, nc = vi ? np : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ct += __shfl_xor_sync(FULL, ct, o);
+        nc += __shfl_xor_sync(FULL, nc, o);
+      }
+      if (lane == 0) {
+        atomicAdd(a.units, (unsigned long long)ct);
+        atomicAdd(a.units + 1, (unsigned long long)nc);
+      }
+    }
+  }
+}
+
+template <class P, bool COUNT>
+int launch_listeval(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
+  auto kern = k_listeval<P, COUNT>;
+  int dev = 0, nsm = 0, per_sm = 0;
+  SPH_CUDA(cudaGetDevice(&dev));
+  SPH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  SPH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LE_WARPS * 32, 0));
+  if (per_sm <= 0) per_sm = 1;
+  const long long ngrp = (a.n + 31) >> 5;
+  int grid = (int)std::min<long long>((long long)nsm * per_sm, div_up(ngrp, LE_WARPS));
+  if (grid < 1) grid = 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profile) {
+    if (c->ev_pending.size() >= 2048) SPH_TRY(prof_resolve(c));
+    a.units = c->prof_units.as<unsigned long long>() + 2 * c->ev_pending.size();
+    SPH_CUDA(cudaMemsetAsync(a.units, 0, 2 * sizeof(unsigned long long), s));
+    e0 = ev_get(c);
+    e1 = ev_get(c);
+    SPH_CUDA(cudaEventRecord(e0, s));
+  }
+  { kern<<<grid, LE_WARPS * 32, 0, s>>>(a); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  if (c->profile) {
+    SPH_CUDA(cudaEventRecord(e1, s));
+    c->ev_pending.push_back({c->cur_phase, e0, e1});
+  }
+  return SPH_OK;
+}
+
+// list mode per phase (bit k of sweep_lists for phase k); byte lists hold
+// slots below 256
+template <class P, bool COUNT>
+int launch(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
+  a.cap = c->sweep_cap;
+  a.bmax = c->prm.block_max;
+  const bool list = a.cap <= 256 && (a.fl_list != nullptr ||
+                                     (c->cur_phase < PH_DUMP_DENSITY &&
+                                      ((c->prm.sweep_lists >> c->cur_phase) & 1)));
+  return list ? launch_shape<P, COUNT, true>(c, a, s) : launch_shape<P, COUNT, false>(c, a, s);
+}
+
+// a phase over (a subset of) the force pairs: from the pair lists when the
+// force sweep recorded them for the current h, plus a masked sweep of the
+// particles whose list overflowed (it returns at once when none did);
+// otherwise a plain sweep
+template <class P, bool COUNT>
+int launch_pairs(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
+  if (!c->fl_valid) return launch<P, COUNT>(c, a, s);
+  a.fl_list = c->fl_list.as<unsigned>();
+  a.fl_cnt = c->fl_cnt.as<int>();
+  a.fl_K = c->fl_K;
+  a.p_et = c->p_et.as<float>();
+  a.n = c->n;
+  {
+    const int r = launch_listeval<P, COUNT>(c, a, s);
+    if (r != SPH_OK) return r;
+  }
+  SweepArgs f = a;
+  f.fl_list = nullptr;
+  f.pflag = c->fl_flag.as<int>();
+  f.blk_active = c->fl_blk.as<int>();
+  f.run_if = c->fl_over.as<int>();
+  return launch<P, COUNT>(c, f, s);
 }
 
 }  // namespace
@@ -833,21 +1089,46 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
       return counting ? launch<PDensity, true>(c, a, s) : launch<PDensity, false>(c, a, s);
     case PH_DENSITY_D2:
       a.o0 = c->d2rho.as<float>();
-      return counting ? launch<PDensityD2, true>(c, a, s) : launch<PDensityD2, false>(c, a, s);
+      return counting ? launch_pairs<PDensityD2, true>(c, a, s)
+                      : launch_pairs<PDensityD2, false>(c, a, s);
     case PH_FORCE:
       a.o4 = c->acc4.as<float4>();
+      c->fl_valid = false;
+      if (c->prm.pair_list_cap > 0 && c->sweep_cap <= 256 && c->n < (1ll << 27)) {
+        const long long ng = (c->n + 31) >> 5;
+        SPH_TRY(dbuf_ensure(c->fl_list, sizeof(unsigned) * (size_t)ng * 32 * c->prm.pair_list_cap));
+        SPH_TRY(dbuf_ensure(c->fl_cnt, sizeof(int) * (size_t)c->n));
+        SPH_TRY(dbuf_ensure(c->fl_flag, sizeof(int) * (size_t)c->n));
+        SPH_TRY(dbuf_ensure(c->fl_blk, sizeof(int) * (size_t)c->nblock));
+        SPH_TRY(dbuf_ensure(c->fl_over, 64));
+        SPH_CUDA(cudaMemsetAsync(c->fl_blk.p, 0, sizeof(int) * (size_t)c->nblock, s));
+        SPH_CUDA(cudaMemsetAsync(c->fl_over.p, 0, sizeof(int), s));
+        c->fl_K = c->prm.pair_list_cap;
+        a.fl_list = c->fl_list.as<unsigned>();
+        a.fl_cnt = c->fl_cnt.as<int>();
+        a.fl_flag = c->fl_flag.as<int>();
+        a.fl_blk = c->fl_blk.as<int>();
+        a.fl_over = c->fl_over.as<int>();
+        a.fl_K = c->fl_K;
+        const int r = counting ? launch<PForce, true>(c, a, s) : launch<PForce, false>(c, a, s);
+        if (r != SPH_OK) return r;
+        c->fl_valid = true;
+        return SPH_OK;
+      }
       return counting ? launch<PForce, true>(c, a, s) : launch<PForce, false>(c, a, s);
     case PH_FORCE_ADJ:
       a.adj4 = c->adj4.as<float4>();
       a.o4 = c->g_x4.as<float4>();
       a.o0 = c->g_A.as<float>();
       a.o1 = c->g_h_s.as<float>();
-      return counting ? launch<PForceAdj, true>(c, a, s) : launch<PForceAdj, false>(c, a, s);
+      return counting ? launch_pairs<PForceAdj, true>(c, a, s)
+                      : launch_pairs<PForceAdj, false>(c, a, s);
     case PH_DENSITY_ADJ:
       a.adj4 = c->adj4.as<float4>();
       a.adj4b = c->adj4b.as<float4>();
       a.o4 = c->g_x4.as<float4>();
-      return counting ? launch<PDensityAdj, true>(c, a, s) : launch<PDensityAdj, false>(c, a, s);
+      return counting ? launch_pairs<PDensityAdj, true>(c, a, s)
+                      : launch_pairs<PDensityAdj, false>(c, a, s);
     case PH_DUMP_DENSITY:
     case PH_DUMP_FORCE:
       a.perm = c->perm.as<int>();
@@ -856,8 +1137,10 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
       a.dump_n = c->counters.as<unsigned long long>();
       a.dump_cap = c->dump_cap;
       a.kahan = 0;
-      return phase == PH_DUMP_DENSITY ? launch<PDump<0>, false>(c, a, s)
-                                      : launch<PDump<1>, false>(c, a, s);
+      a.cap = c->sweep_cap;
+      a.bmax = c->prm.block_max;
+      return phase == PH_DUMP_DENSITY ? launch_shape<PDump<0>, false, false>(c, a, s)
+                                      : launch_shape<PDump<1>, false, false>(c, a, s);
     default:
       return SPH_ERR_INVALID_ARG;
   }

@@ -93,3 +93,29 @@ def test_adjoint_with_velocities_and_dudt_upstream():
     res = _grad_check(d, v=d["v"], g_du=True)
     for k, (rel, elem) in res.items():
         assert rel <= 1e-3, (k, rel)
+
+
+@pytest.mark.parametrize("cap", [0, 40])
+def test_pair_lists_match_sweeps(cap):
+    """The force sweep records per-particle pair lists that the d2rho/dh2,
+    force-adjoint and density-adjoint phases read instead of sweeping; a
+    particle with more pairs than the capacity is swept.  Without lists
+    (cap 0), with lists that overflow for part of the particles (cap 40)
+    and with roomy lists, the gradients agree to FP32 summation order."""
+    d = C.random_box(20000, 7, "clumped", v_sigma=0.1)
+    rng = np.random.default_rng(6)
+    gdu = _t(rng.normal(size=d["x"].shape[0]).astype(np.float32))
+    out = {}
+    for K in (256, cap):
+        s = _sph(pair_list_cap=K)
+        s.build(_t(d["x"]))
+        den = s.density(_t(d["m"]))
+        acc, _, cnt = s.force(_t(d["u"]), _t(d["v"]), count=True)
+        g = s.adjoint(2.0 * (den["rho"] - 1.0), 2.0 * acc, gdu)
+        out[K] = [t.cpu().numpy().astype(np.float64).reshape(-1) for t in g]
+        if K == 40:
+            # the capacity is below the largest pair count: some lists overflowed
+            assert int(cnt.max()) + 1 > 40
+    for a, b in zip(out[256], out[cap]):
+        rms = np.sqrt(np.mean(a ** 2))
+        assert np.max(np.abs(a - b)) <= 1e-5 * rms + 1e-6 * np.abs(a).max()
