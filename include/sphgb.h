@@ -130,6 +130,11 @@ typedef struct sph_stats {
   int32_t unconverged;       /* particles left unconverged by the last sph_density */
   int32_t sweep_grid;        /* CTAs of the last sweep launch */
   int32_t sweep_threads;     /* threads per CTA of the sweep launches */
+  /* build wall time per stage while profiling is on (the stream is synchronised at each
+   * stage boundary): 0 Morton order, 1 h estimate, 2 octree, 3 pair tasks, 4 blocks and
+   * block sorts, 5 hierarchical merge, 6 interaction lists, 7 node h maxima */
+  double build_ms[8];
+  int32_t builds;            /* decompositions built while profiling (rebuilds included) */
 } sph_stats;
 
 /* Fill *p with the defaults listed above. */

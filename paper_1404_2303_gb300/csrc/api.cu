@@ -667,7 +667,9 @@ int sph_profile(sph_ctx* c, int32_t enable) {
     c->prof_n[k] = 0;
     c->prof_units_acc[k] = 0;
     c->prof_cand_acc[k] = 0;
+    c->prof_build_ms[k] = 0;
   }
+  c->prof_builds = 0;
   if (enable) SPH_TRY(dbuf_ensure(c->prof_units, 4096 * sizeof(unsigned long long)));
   c->profile = enable != 0;
   return SPH_OK;
@@ -683,11 +685,19 @@ int sph_get_stats(sph_ctx* c, sph_stats* out) {
     st.sweep_units[k] = (int64_t)c->prof_units_acc[k];
     st.sweep_candidates[k] = (int64_t)c->prof_cand_acc[k];
   }
+  for (int k = 0; k < 8; ++k) st.build_ms[k] = c->prof_build_ms[k];
+  st.builds = c->prof_builds;
   st.sweep_grid = c->sweep_grid;
   st.sweep_threads = c->sweep_threads;
   st.n = c->n;
   st.nbox = c->nbox;
   st.ncell = c->ncell;
+  if (c->built && c->nleaf_dev.p) {
+    int nl = 0;
+    SPH_CUDA(cudaDeviceSynchronize());
+    SPH_CUDA(cudaMemcpy(&nl, c->nleaf_dev.p, sizeof(int), cudaMemcpyDeviceToHost));
+    c->nleaf = nl;
+  }
   st.nleaf = c->nleaf;
   st.nblock = c->nblock;
   st.nself = c->nself;

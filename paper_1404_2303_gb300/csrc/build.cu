@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <chrono>
+
 #include "geom.cuh"
 #include "internal.cuh"
 
@@ -355,68 +357,100 @@ __global__ void k_make_blocks(int ncell, const int* first, const int* count, con
 
 // ---------------------------------------------------------------- sorts
 // (key, global index) order: ties cannot occur because indices are distinct
-constexpr int SORT_MAX = 256;
 
 __device__ __forceinline__ bool kv_less(float ka, int ia, float kb, int ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
 
-// one warp per (block, direction): bitonic sort of (key, index) pairs in
-// shared memory, padded to a power of two >= 32
+// One warp per block sorts it along all 13 directions: the block's
+// positions are loaded once (R per lane, padded to 32 R with +inf keys) and
+// each direction's (key, index) pairs are sorted by a bitonic network in
+// registers: partners 32 or more apart sit in the same lane, closer ones are
+// exchanged with shuffles.
 constexpr int WS_WARPS = 8;
+
+template <int R>
+__device__ __forceinline__ void sort_block_dirs(int f, int c, const float4* pos4, float* s_key,
+                                                int* s_idx) {
+  const int lane = threadIdx.x & 31;
+  constexpr int NP = 32 * R;
+  float px[R], py[R], pz[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int t = r * 32 + lane;
+    if (t < c) {
+      const float4 p = pos4[f + t];
+      px[r] = p.x; py[r] = p.y; pz[r] = p.z;
+    } else {
+      px[r] = py[r] = pz[r] = 0.f;
+    }
+  }
+  for (int d = 0; d < SPH_NDIR; ++d) {
+    float ux, uy, uz;
+    dir_unit(d, ux, uy, uz);
+    float k[R];
+    int x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int t = r * 32 + lane;
+      k[r] = t < c ? sort_key(px[r], py[r], pz[r], ux, uy, uz) : __int_as_float(0x7f800000);
+      x[r] = t < c ? f + t : 0x7fffffff;
+    }
+#pragma unroll
+    for (int kk = 2; kk <= NP; kk <<= 1) {
+#pragma unroll
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        if (j >= 32) {
+          const int js = j >> 5;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if (r & js) continue;
+            const int r2 = r | js;
+            const bool up = ((r * 32 + lane) & kk) == 0;
+            const bool sw = up ? kv_less(k[r2], x[r2], k[r], x[r]) : kv_less(k[r], x[r], k[r2], x[r2]);
+            if (sw) {
+              const float tk = k[r]; k[r] = k[r2]; k[r2] = tk;
+              const int tx = x[r]; x[r] = x[r2]; x[r2] = tx;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float ok = __shfl_xor_sync(0xffffffffu, k[r], j);
+            const int ox = __shfl_xor_sync(0xffffffffu, x[r], j);
+            const bool lower = (lane & j) == 0;
+            const bool up = ((r * 32 + lane) & kk) == 0;
+            // the lower partner keeps the smaller pair in ascending runs
+            const bool other_less = kv_less(ok, ox, k[r], x[r]);
+            const bool take = (lower == up) ? other_less : !other_less;
+            if (take) { k[r] = ok; x[r] = ox; }
+          }
+        }
+      }
+    }
+    const long long o = 13ll * f + (long long)d * c;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int t = r * 32 + lane;
+      if (t < c) {
+        s_key[o + t] = k[r];
+        s_idx[o + t] = x[r];
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(WS_WARPS * 32)
     k_sort_blocks_warp(int nblock, const int* b_first, const int* b_count, const float4* pos4,
                        float* s_key, int* s_idx) {
-  __shared__ float sk[WS_WARPS][SORT_MAX];
-  __shared__ int si[WS_WARPS][SORT_MAX];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long items = (long long)nblock * SPH_NDIR;
-  for (long long item = (long long)blockIdx.x * WS_WARPS + warp; item < items;
-       item += (long long)gridDim.x * WS_WARPS) {
-    const int b = (int)(item / SPH_NDIR), d = (int)(item % SPH_NDIR);
+  const int warp = threadIdx.x >> 5;
+  for (long long b = (long long)blockIdx.x * WS_WARPS + warp; b < nblock;
+       b += (long long)gridDim.x * WS_WARPS) {
     const int f = b_first[b], c = b_count[b];
-    float ux, uy, uz;
-    dir_unit(d, ux, uy, uz);
-    int np2 = 32;
-    while (np2 < c) np2 <<= 1;
-    float* K = sk[warp];
-    int* X = si[warp];
-    for (int t = lane; t < np2; t += 32) {
-      if (t < c) {
-        float4 p = pos4[f + t];
-        K[t] = sort_key(p.x, p.y, p.z, ux, uy, uz);
-        X[t] = f + t;
-      } else {
-        K[t] = __int_as_float(0x7f800000);
-        X[t] = 0x7fffffff;
-      }
-    }
-    __syncwarp();
-    for (int k = 2; k <= np2; k <<= 1) {
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int t = lane; t < np2; t += 32) {
-          int p = t ^ j;
-          if (p > t) {
-            bool up = (t & k) == 0;
-            float ka = K[t], kb = K[p];
-            int ia = X[t], ib = X[p];
-            bool sw = up ? kv_less(kb, ib, ka, ia) : kv_less(ka, ia, kb, ib);
-            if (sw) {
-              K[t] = kb; K[p] = ka;
-              X[t] = ib; X[p] = ia;
-            }
-          }
-        }
-        __syncwarp();
-      }
-    }
-    const long long o = 13ll * f + (long long)d * c;
-    for (int t = lane; t < c; t += 32) {
-      s_key[o + t] = K[t];
-      s_idx[o + t] = X[t];
-    }
-    __syncwarp();
+    if (c <= 32) sort_block_dirs<1>(f, c, pos4, s_key, s_idx);
+    else if (c <= 64) sort_block_dirs<2>(f, c, pos4, s_key, s_idx);
+    else if (c <= 128) sort_block_dirs<4>(f, c, pos4, s_key, s_idx);
+    else sort_block_dirs<8>(f, c, pos4, s_key, s_idx);
   }
 }
 
@@ -445,34 +479,63 @@ __global__ void k_need_down(int g0, int g1, const int* child0, int* need) {
   for (int k = 0; k < 8; ++k) atomicOr(&need[c0 + k], nd);
 }
 
+// A node is listed (its 13 sorted lists exist) when it holds at most
+// LIST_CAP particles and every descendant is listed; a leaf also needs at
+// most LIST_SUB blocks.  Its lists are then merged in shared memory from its
+// children's (or its blocks') lists.  A task that names an unlisted node
+// reaches its particles through the listed descendants, or through the
+// blocks of an unlisted leaf (blocks always have lists).  ex[node] counts the
+// interaction-list entries a reference to the node expands to.
+constexpr int LIST_CAP = 4096;
+constexpr int LIST_SUB = 16;
+
+__global__ void k_listed(int g0, int g1, const int* child0, const int* count, const int* nblk,
+                         int* listed, int* ex) {
+  int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g1) return;
+  const int cnt = count[node];
+  if (cnt == 0) {
+    listed[node] = 1;
+    ex[node] = 0;
+    return;
+  }
+  const int c0 = child0[node];
+  if (c0 < 0) {
+    const bool L = cnt <= LIST_CAP && nblk[node] <= LIST_SUB;
+    listed[node] = L ? 1 : 0;
+    ex[node] = L ? 1 : nblk[node];
+    return;
+  }
+  bool all = cnt <= LIST_CAP;
+  int e = 0;
+  for (int k = 0; k < 8; ++k) {
+    all = all && listed[c0 + k] != 0;
+    e += ex[c0 + k];
+  }
+  listed[node] = all ? 1 : 0;
+  ex[node] = all ? 1 : e;
+}
+
 __global__ void k_sort_size(int ncell, const int* need, const int* child0, const int* nblk,
-                            const int* count, long long* sz) {
+                            const int* count, const int* listed, long long* sz) {
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= ncell) return;
   bool alias = child0[id] < 0 && nblk[id] == 1;
-  sz[id] = (need[id] != 0 && !alias && count[id] > 0) ? 13ll * count[id] : 0;
+  sz[id] = (need[id] != 0 && !alias && count[id] > 0 && listed[id]) ? 13ll * count[id] : 0;
 }
 
 __global__ void k_sort_base(int ncell, const int* need, const int* child0, const int* nblk,
-                            const int* first, const int* count, const long long* off,
-                            long long base, long long* sbase) {
+                            const int* first, const int* count, const int* listed,
+                            const long long* off, long long base, long long* sbase) {
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= ncell) return;
   bool alias = child0[id] < 0 && nblk[id] == 1;
   if (alias) sbase[id] = 13ll * first[id];
-  else if (need[id] != 0 && count[id] > 0) sbase[id] = base + off[id];
+  else if (need[id] != 0 && count[id] > 0 && listed[id]) sbase[id] = base + off[id];
   else sbase[id] = -1;
 }
 
 
-__device__ __forceinline__ int count_less(const float* k, const int* ix, int n, float kv, int iv) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (kv_less(k[mid], ix[mid], kv, iv)) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
 
 // ---------------------------------------------------------------- interaction lists
@@ -503,46 +566,121 @@ __global__ void k_pair_sortlists(int ncell, const int* off, const int* deg, int*
   }
 }
 
+// the other cell of the k-th pair task listed for node a, with the offset
+// from a to it
+__device__ __forceinline__ int pair_other(const int* alist, const int4* pairs, int v, int& ox,
+                                          int& oy, int& oz, int& px, int& py, int& pz) {
+  int4 tk = pairs[v >> 1];
+  unpack_pair(tk.z, ox, oy, oz, px, py, pz);
+  if (v & 1) {
+    ox = -ox; oy = -oy; oz = -oz;
+    px = -px; py = -py; pz = -pz;
+    return tk.x;
+  }
+  return tk.y;
+}
+
 __global__ void k_block_ndt(int nblock, const int* b_leaf, const int* parent, const int* deg,
-                            long long* ndt) {
+                            const int* aoff, const int* alist, const int4* pairs,
+                            const int* listed, const int* ex, const int* nblk, long long* ndt) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblock) return;
-  long long c = 1;
-  for (int a = b_leaf[b]; a >= 0; a = parent[a]) c += deg[a];
+  const int leaf = b_leaf[b];
+  long long c = listed[leaf] ? 1 : nblk[leaf];
+  for (int a = leaf; a >= 0; a = parent[a]) {
+    for (int k = 0; k < deg[a]; ++k) {
+      int ox, oy, oz, px, py, pz;
+      const int other = pair_other(alist, pairs, alist[aoff[a] + k], ox, oy, oz, px, py, pz);
+      c += ex[other];
+    }
+  }
   ndt[b] = c;
+}
+
+// Appends the entries a reference to node x expands to: x itself when
+// listed, else the blocks of an unlisted leaf, else (depth first) those of
+// its children.  Block targets are stored as -1 - block.
+__device__ __forceinline__ long long emit_target(int x, int code, float4 sh, long long e,
+                                                 const int* listed, const int* child0,
+                                                 const int* parent, const int* count,
+                                                 const int* nblk, const int* blk0,
+                                                 const int* b_count, int* dt_cj, int* dt_code,
+                                                 float4* dt_shift, double& cost, double wi) {
+  if (count[x] == 0) return e;
+  if (listed[x]) {
+    dt_cj[e] = x; dt_code[e] = code; dt_shift[e] = sh;
+    cost += wi * (double)min(count[x], 4096);
+    return e + 1;
+  }
+  if (child0[x] < 0) {
+    for (int k = 0; k < nblk[x]; ++k) {
+      const int bj = blk0[x] + k;
+      dt_cj[e] = -1 - bj; dt_code[e] = code; dt_shift[e] = sh;
+      cost += wi * (double)b_count[bj];
+      ++e;
+    }
+    return e;
+  }
+  // depth-first walk of the unlisted subtree: idx[l] is the next child at depth l
+  int idx[32];
+  int node = x, l = 0;
+  idx[0] = 0;
+  while (l >= 0) {
+    if (idx[l] == 8) {
+      --l;
+      if (l >= 0) {
+        node = parent[node];
+        ++idx[l];
+      }
+      continue;
+    }
+    const int ch = child0[node] + idx[l];
+    if (count[ch] == 0) {
+      ++idx[l];
+    } else if (listed[ch]) {
+      dt_cj[e] = ch; dt_code[e] = code; dt_shift[e] = sh;
+      cost += wi * (double)min(count[ch], 4096);
+      ++e;
+      ++idx[l];
+    } else if (child0[ch] < 0) {
+      for (int k = 0; k < nblk[ch]; ++k) {
+        const int bj = blk0[ch] + k;
+        dt_cj[e] = -1 - bj; dt_code[e] = code; dt_shift[e] = sh;
+        cost += wi * (double)b_count[bj];
+        ++e;
+      }
+      ++idx[l];
+    } else {
+      node = ch;
+      idx[++l] = 0;
+    }
+  }
+  return e;
 }
 
 __global__ void k_block_dts(int nblock, const int* b_leaf, const int* b_count, const int* parent,
                             const int* deg, const int* aoff, const int* alist, const int4* pairs,
                             const int* ntop, const int4* ijk, const int* box, const double* Ls,
-                            const int* box_t, const int* ncount, const long long* dtoff,
-                            int* dt_cj, int* dt_code, float4* dt_shift, unsigned long long* cost) {
+                            const int* box_t, const int* ncount, const int* listed,
+                            const int* child0, const int* nblk, const int* blk0,
+                            const long long* dtoff, int* dt_cj, int* dt_code, float4* dt_shift,
+                            unsigned long long* cost) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblock) return;
   long long e = dtoff[b];
-  int leaf = b_leaf[b];
-  dt_cj[e] = leaf;
-  dt_code[e] = SPH_SELF_DIR | (1 << 8);
-  dt_shift[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-  double c = (double)b_count[b] * (double)min(ncount[leaf], 4096);
-  ++e;
+  const int leaf = b_leaf[b];
+  const double wb = (double)b_count[b];
+  double c = 0;
+  e = emit_target(leaf, SPH_SELF_DIR | (1 << 8), make_float4(0.f, 0.f, 0.f, 0.f), e, listed, child0,
+                  parent, ncount, nblk, blk0, b_count, dt_cj, dt_code, dt_shift, c, wb);
   int bx = box[leaf];
   double L = Ls[bx];
   double et = L / (double)(1 << box_t[bx]);
   int4 ta = ijk[ntop[leaf]];
   for (int a = leaf; a >= 0; a = parent[a]) {
     for (int k = 0; k < deg[a]; ++k) {
-      int v = alist[aoff[a] + k];
-      int4 tk = pairs[v >> 1];
-      int side = v & 1;
       int ox, oy, oz, px, py, pz;
-      unpack_pair(tk.z, ox, oy, oz, px, py, pz);
-      int other = tk.y;
-      if (side) {
-        other = tk.x;
-        ox = -ox; oy = -oy; oz = -oz;
-        px = -px; py = -py; pz = -pz;
-      }
+      const int other = pair_other(alist, pairs, alist[aoff[a] + k], ox, oy, oz, px, py, pz);
       int oc = off_code(ox, oy, oz);
       int dir, sgn;
       if (oc > 13) { dir = oc - 14; sgn = 1; } else { dir = 12 - oc; sgn = -1; }
@@ -550,11 +688,9 @@ __global__ void k_block_dts(int nblock, const int* b_leaf, const int* b_count, c
       float sx = (float)((tb.x - ta.x) * et + px * L);
       float sy = (float)((tb.y - ta.y) * et + py * L);
       float sz = (float)((tb.z - ta.z) * et + pz * L);
-      dt_cj[e] = other;
-      dt_code[e] = dir | ((sgn + 1) << 8);
-      dt_shift[e] = make_float4(sx, sy, sz, 0.f);
-      c += (double)b_count[b] * (double)min(ncount[other], 4096) * 0.5;
-      ++e;
+      e = emit_target(other, dir | ((sgn + 1) << 8), make_float4(sx, sy, sz, 0.f), e, listed,
+                      child0, parent, ncount, nblk, blk0, b_count, dt_cj, dt_code, dt_shift, c,
+                      0.5 * wb);
     }
   }
   unsigned cc = c > 4.0e9 ? 0xffffffffu : (unsigned)c;
@@ -687,8 +823,15 @@ __global__ void k_box_hmax(long long n, const long long* off, int nbox, const fl
 // index space; each thread ranks one element of one sub-list (child cell or
 // leaf block) against the node's other sub-lists by binary search.
 __device__ __forceinline__ bool mergeable(int node, const int* need, const int* child0,
-                                          const int* nblk, const int* count) {
-  return need[node] != 0 && count[node] > 0 && !(child0[node] < 0 && nblk[node] <= 1);
+                                          const int* nblk, const int* count, const int* listed) {
+  return need[node] != 0 && count[node] > 0 && listed[node] && !(child0[node] < 0 && nblk[node] <= 1);
+}
+
+__global__ void k_count_positive(int n, const int* v, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool p = i < n && v[i] > 0;
+  unsigned m = __ballot_sync(0xffffffffu, p);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(out, __popc(m));
 }
 
 __global__ void k_gather_i64(int n, const int* idx, const long long* in, long long* out) {
@@ -696,81 +839,100 @@ __global__ void k_gather_i64(int n, const int* idx, const long long* in, long lo
   if (i < n) out[i] = in[idx[i]];
 }
 
+// merge work per node: one (node, direction) segment per needed direction
+// of a listed node, merged by one CTA in shared memory (k_merge_smem)
+constexpr int MS_CAP = LIST_CAP;
+constexpr int MS_SUB = LIST_SUB;
+constexpr int MS_TPB = 256;
+
 __global__ void k_merge_count(int g0, int g1, const int* need, const int* child0, const int* nblk,
-                              const int* count, long long* elems) {
+                              const int* count, const int* listed, long long* segs) {
   int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g1) return;
-  elems[node - g0] = mergeable(node, need, child0, nblk, count)
-                         ? (long long)count[node] * __popc(need[node])
-                         : 0;
+  segs[node - g0] = mergeable(node, need, child0, nblk, count, listed) ? __popc(need[node]) : 0;
 }
 
-__global__ void k_merge_flat(int g0, int ng, const long long* off, long long base, long long total,
-                             const int* need, const int* child0, const int* count, const int* nblk,
-                             const int* blk0, const int* b_first, const int* b_count,
-                             const long long* sbase, float* s_key, int* s_idx) {
-  for (long long el = blockIdx.x * (long long)blockDim.x + threadIdx.x; el < total;
-       el += (long long)gridDim.x * blockDim.x) {
-    const long long e = base + el;
-    // node: last index with off[i] <= e
+__device__ __forceinline__ int count_less_s(const float* k, const int* ix, int n, float kv, int iv) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (kv_less(k[mid], ix[mid], kv, iv)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// one CTA per (node, direction) segment: the sub-lists (children's or the
+// leaf's blocks' lists of that direction) are loaded side by side into
+// shared memory and every element is ranked against the other sub-lists
+__global__ void __launch_bounds__(MS_TPB)
+    k_merge_smem(int g0, int ng, const long long* soff, long long seg0, const int* need,
+                 const int* child0, const int* count, const int* nblk, const int* blk0,
+                 const int* b_first, const int* b_count, const long long* sbase, float* s_key,
+                 int* s_idx) {
+  __shared__ float K[MS_CAP];
+  __shared__ int X[MS_CAP];
+  __shared__ int so[MS_SUB + 1];
+  __shared__ long long sb[MS_SUB];
+  __shared__ long long dst0;
+  __shared__ int nsub_s;
+  if (threadIdx.x == 0) {
+    const long long sg = seg0 + blockIdx.x;
     int lo = 0, hi = ng;
     while (hi - lo > 1) {
       int mid = (lo + hi) >> 1;
-      if (off[mid] <= e) lo = mid; else hi = mid;
+      if (soff[mid] <= sg) lo = mid; else hi = mid;
     }
-    int node = g0 + lo;
-    long long loc = e - off[lo];
-    int cnt = count[node];
-    int slot = (int)(loc / cnt);
-    int l = (int)(loc - (long long)slot * cnt);
+    const int node = g0 + lo;
     int nd = need[node];
-    int d = 0;
-    for (int k = 0; k <= slot; ++k) {
-      d = __ffs(nd) - 1;
-      nd &= nd - 1;
-    }
+    for (long long k = sg - soff[lo]; k > 0; --k) nd &= nd - 1;
+    const int d = __ffs(nd) - 1;
     const bool leaf = child0[node] < 0;
     const int nsub = leaf ? nblk[node] : 8;
-    // locate the element's sub-list
-    int s = 0, base = 0;
-    long long sb = 0;
-    int sc = 0;
-    for (s = 0; s < nsub; ++s) {
+    int acc = 0;
+    for (int q = 0; q < nsub; ++q) {
+      int sc;
+      long long base;
       if (leaf) {
-        int bi = blk0[node] + s;
+        const int bi = blk0[node] + q;
         sc = b_count[bi];
-        sb = 13ll * b_first[bi] + (long long)d * sc;
+        base = 13ll * b_first[bi] + (long long)d * sc;
       } else {
-        int ch = child0[node] + s;
+        const int ch = child0[node] + q;
         sc = count[ch];
-        sb = sc > 0 ? sbase[ch] + (long long)d * sc : 0;
+        base = sc > 0 ? sbase[ch] + (long long)d * sc : 0;
       }
-      if (l < base + sc) break;
-      base += sc;
+      so[q] = acc;
+      sb[q] = base;
+      acc += sc;
     }
-    int li = l - base;
-    float kv = s_key[sb + li];
-    int iv = s_idx[sb + li];
-    int rank = li;
+    so[nsub] = acc;
+    nsub_s = nsub;
+    dst0 = sbase[node] + (long long)d * count[node];
+  }
+  __syncthreads();
+  const int nsub = nsub_s;
+  for (int q = 0; q < nsub; ++q) {
+    const int o = so[q], c = so[q + 1] - o;
+    const long long b = sb[q];
+    for (int e = threadIdx.x; e < c; e += MS_TPB) {
+      K[o + e] = s_key[b + e];
+      X[o + e] = s_idx[b + e];
+    }
+  }
+  __syncthreads();
+  const int total = so[nsub];
+  for (int e = threadIdx.x; e < total; e += MS_TPB) {
+    int q = 0;
+    while (e >= so[q + 1]) ++q;
+    const float kv = K[e];
+    const int iv = X[e];
+    int rank = e - so[q];
     for (int o = 0; o < nsub; ++o) {
-      if (o == s) continue;
-      long long ob;
-      int oc;
-      if (leaf) {
-        int bi = blk0[node] + o;
-        oc = b_count[bi];
-        ob = 13ll * b_first[bi] + (long long)d * oc;
-      } else {
-        int ch = child0[node] + o;
-        oc = count[ch];
-        if (oc == 0) continue;
-        ob = sbase[ch] + (long long)d * oc;
-      }
-      rank += count_less(s_key + ob, s_idx + ob, oc, kv, iv);
+      if (o == q) continue;
+      rank += count_less_s(K + so[o], X + so[o], so[o + 1] - so[o], kv, iv);
     }
-    long long dst = sbase[node] + (long long)d * cnt + rank;
-    s_key[dst] = kv;
-    s_idx[dst] = iv;
+    s_key[dst0 + rank] = kv;
+    s_idx[dst0 + rank] = iv;
   }
 }
 
@@ -1108,6 +1270,18 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
                                                    c->b_first.as<int>(), c->b_count.as<int>(),
                                                    c->b_leaf.as<int>(), blk0); note_launch(); }
   SPH_CUDA(cudaGetLastError());
+  // listed nodes and expansion counts, bottom-up
+  SPH_TRY(dbuf_ensure(c->n_listed, sizeof(int) * (ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->n_ex, sizeof(int) * (ncell + 1)));
+  int* listed = c->n_listed.as<int>();
+  int* nex = c->n_ex.as<int>();
+  for (int g = (int)c->gen_start.size() - 2; g >= 0; --g) {
+    const int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
+    if (g1 <= g0) continue;
+    { k_listed<<<div_up(g1 - g0, TPB), TPB, 0, s>>>(g0, g1, c->n_child0.as<int>(),
+                                                   c->n_count.as<int>(), nblk, listed, nex); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
   // block sorts: lists of all 13 directions at [13 first, 13 (first + count))
   // needs
   int* need = c->n_need.as<int>();
@@ -1128,7 +1302,7 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
   long long* szp = sz.as<long long>();
   long long* szo = szp + (ncell + 1);
   { k_sort_size<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, need, c->n_child0.as<int>(), nblk,
-                                                 c->n_count.as<int>(), szp); note_launch(); }
+                                                 c->n_count.as<int>(), listed, szp); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   SPH_TRY(scan_exclusive_i64(szp, szo, ncell, szo + ncell, c->scan_tmp, s));
   long long extra = 0;
@@ -1138,52 +1312,52 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
   SPH_TRY(dbuf_ensure(c->s_idx, sizeof(int) * (size_t)c->sorted_entries));
   SPH_TRY(dbuf_ensure(c->n_sbase, sizeof(long long) * (ncell + 1)));
   { k_sort_base<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, need, c->n_child0.as<int>(), nblk,
-                                                 c->n_first.as<int>(), c->n_count.as<int>(), szo,
-                                                 13ll * n, c->n_sbase.as<long long>()); note_launch(); }
+                                                 c->n_first.as<int>(), c->n_count.as<int>(), listed,
+                                                 szo, 13ll * n, c->n_sbase.as<long long>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   if (nblock > 0) {
-    int grid = (int)std::min<long long>(div_up((long long)nblock * SPH_NDIR, WS_WARPS), 152ll * 32);
+    int grid = (int)std::min<long long>(div_up((long long)nblock, WS_WARPS), 152ll * 16);
     { k_sort_blocks_warp<<<grid, WS_WARPS * 32, 0, s>>>(nblock, c->b_first.as<int>(),
                                                        c->b_count.as<int>(), c->pos4.as<float4>(),
                                                        c->s_key.as<float>(), c->s_idx.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
   }
+  SPH_TRY(build_mark(c, s, 4));
   {
-    // merge elements of every cell in one scan (cells are numbered by
+    // merge segments of every cell in one scan (cells are numbered by
     // generation), one host read of the per-generation offsets, then the
     // generations from the deepest up (children before parents)
     const int ng_all = ncell;
-    SPH_TRY(dbuf_ensure(sz, sizeof(long long) * (size_t)(2 * ng_all + 2 + 2 * c->gen_start.size())));
-    long long* el = sz.as<long long>();
-    long long* eo = el + (ng_all + 1);
-    long long* ego = eo + (ng_all + 1);
-    { k_merge_count<<<div_up(ng_all, TPB), TPB, 0, s>>>(0, ng_all, need, c->n_child0.as<int>(), nblk,
-                                                       c->n_count.as<int>(), el); note_launch(); }
-    SPH_CUDA(cudaGetLastError());
-    SPH_TRY(scan_exclusive_i64(el, eo, ng_all, eo + ng_all, c->scan_tmp, s));
     const int ngen = (int)c->gen_start.size();
+    SPH_TRY(dbuf_ensure(sz, sizeof(long long) * (size_t)(2 * (ng_all + 1) + ngen + 2)));
+    long long* sgc = sz.as<long long>();
+    long long* sgo = sgc + (ng_all + 1);
+    long long* gofs = sgo + (ng_all + 1);
+    { k_merge_count<<<div_up(ng_all, TPB), TPB, 0, s>>>(0, ng_all, need, c->n_child0.as<int>(), nblk,
+                                                       c->n_count.as<int>(), listed, sgc); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    SPH_TRY(scan_exclusive_i64(sgc, sgo, ng_all, sgo + ng_all, c->scan_tmp, s));
     SPH_TRY(dbuf_ensure(c->tmp_a, sizeof(int) * (size_t)ngen + 64));
     SPH_CUDA(cudaMemcpyAsync(c->tmp_a.p, c->gen_start.data(), sizeof(int) * ngen,
                              cudaMemcpyHostToDevice, s));
-    { k_gather_i64<<<div_up(ngen, TPB), TPB, 0, s>>>(ngen, c->tmp_a.as<int>(), eo, ego); note_launch(); }
+    { k_gather_i64<<<div_up(ngen, TPB), TPB, 0, s>>>(ngen, c->tmp_a.as<int>(), sgo, gofs); note_launch(); }
     SPH_CUDA(cudaGetLastError());
     std::vector<long long> goff(ngen);
-    SPH_CUDA(cudaMemcpyAsync(goff.data(), ego, sizeof(long long) * ngen, cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaMemcpyAsync(goff.data(), gofs, sizeof(long long) * ngen, cudaMemcpyDeviceToHost, s));
     SPH_CUDA(cudaStreamSynchronize(s));
     for (int g = ngen - 2; g >= 0; --g) {
       const int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
-      const long long total = goff[g + 1] - goff[g];
-      if (g1 <= g0 || total <= 0) continue;
-      int grid = (int)std::min<long long>(div_up(total, TPB), 152ll * 64);
-      { k_merge_flat<<<grid, TPB, 0, s>>>(g0, g1 - g0, eo + g0, goff[g], total, need,
-                                         c->n_child0.as<int>(), c->n_count.as<int>(), nblk, blk0,
-                                         c->b_first.as<int>(), c->b_count.as<int>(),
-                                         c->n_sbase.as<long long>(), c->s_key.as<float>(),
-                                         c->s_idx.as<int>()); note_launch(); }
+      const long long nseg = goff[g + 1] - goff[g];
+      if (g1 <= g0 || nseg <= 0) continue;
+      { k_merge_smem<<<(unsigned)nseg, MS_TPB, 0, s>>>(
+          g0, g1 - g0, sgo + g0, goff[g], need, c->n_child0.as<int>(), c->n_count.as<int>(), nblk,
+          blk0, c->b_first.as<int>(), c->b_count.as<int>(), c->n_sbase.as<long long>(),
+          c->s_key.as<float>(), c->s_idx.as<int>()); note_launch(); }
       SPH_CUDA(cudaGetLastError());
     }
   }
   dbuf_free(sz);
+  SPH_TRY(build_mark(c, s, 5));
 
   // ---- interaction lists per block
   int* deg = c->t_cnt.as<int>();
@@ -1207,8 +1381,9 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
   SPH_TRY(dbuf_ensure(c->b_dtoff, sizeof(long long) * (nblock + 1)));
   SPH_TRY(dbuf_ensure(c->tmp_b, sizeof(long long) * (nblock + 1)));
   { k_block_ndt<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, c->b_leaf.as<int>(),
-                                                  c->n_parent.as<int>(), deg,
-                                                  c->tmp_b.as<long long>()); note_launch(); }
+                                                  c->n_parent.as<int>(), deg, aoff,
+                                                  c->adj_list.as<int>(), c->t_final_pair.as<int4>(),
+                                                  listed, nex, nblk, c->tmp_b.as<long long>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   SPH_TRY(scan_exclusive_i64(c->tmp_b.as<long long>(), c->b_dtoff.as<long long>(), nblock,
                              c->b_dtoff.as<long long>() + nblock, c->scan_tmp, s));
@@ -1225,8 +1400,8 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
       nblock, c->b_leaf.as<int>(), c->b_count.as<int>(), c->n_parent.as<int>(), deg, aoff,
       c->adj_list.as<int>(), c->t_final_pair.as<int4>(), c->n_top.as<int>(), c->n_ijk.as<int4>(),
       c->n_box.as<int>(), c->d_box_L.as<double>(), c->d_box_t.as<int>(), c->n_count.as<int>(),
-      c->b_dtoff.as<long long>(), c->dt_cj.as<int>(), c->dt_code.as<int>(),
-      c->dt_shift.as<float4>(), ck); note_launch(); }
+      listed, c->n_child0.as<int>(), nblk, blk0, c->b_dtoff.as<long long>(), c->dt_cj.as<int>(),
+      c->dt_code.as<int>(), c->dt_shift.as<float4>(), ck); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   // LPT order: descending cost, ties by block id
   int* ov = c->b_order.as<int>();
@@ -1235,20 +1410,29 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
   SPH_TRY(radix_sort_u64(ck, ov, ck + (nblock + 1), ov + (nblock + 1), nblock, 64, c->sort_tmp, s));
   { k_order_from_keys<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, ck, ov); note_launch(); }
   SPH_CUDA(cudaGetLastError());
-  // count leaves (host copy of nblk not needed: leaves = nodes with nblk > 0)
-  {
-    std::vector<int> hb(ncell);
-    SPH_CUDA(cudaMemcpyAsync(hb.data(), nblk, sizeof(int) * ncell, cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaStreamSynchronize(s));
-    int nl = 0;
-    for (int v : hb) nl += v > 0;
-    c->nleaf = nl;
-  }
+  // leaves (nodes with blocks), counted on the device; read with the statistics
+  SPH_TRY(dbuf_ensure(c->nleaf_dev, 64));
+  SPH_CUDA(cudaMemsetAsync(c->nleaf_dev.p, 0, sizeof(int), s));
+  { k_count_positive<<<div_up(ncell, TPB), TPB, 0, s>>>(ncell, nblk, c->nleaf_dev.as<int>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(build_mark(c, s, 6));
+  return SPH_OK;
+}
+
+int build_mark(sph_ctx* c, cudaStream_t s, int k) {
+  if (!c->profile) return SPH_OK;
+  SPH_CUDA(cudaStreamSynchronize(s));
+  const double t = std::chrono::duration<double, std::milli>(
+                       std::chrono::steady_clock::now().time_since_epoch())
+                       .count();
+  if (k >= 0 && k < 8) c->prof_build_ms[k] += t - c->prof_t;
+  c->prof_t = t;
   return SPH_OK;
 }
 
 int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cudaStream_t s) {
   const long long n = c->n;
+  SPH_TRY(build_mark(c, s, -1));
   const int K = c->kbits;
   int boxbits = 0;
   while ((1 << boxbits) < c->nbox) ++boxbits;
@@ -1273,6 +1457,7 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
                                               c->d_box_L.as<double>(), c->nbox, h_guess,
                                               c->xs.as<double>(), c->hguess.as<float>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
+  SPH_TRY(build_mark(c, s, 0));
   if (!h_guess) {
     // count-only octree below a 4^3 top grid gives a local-density h estimate
     c->box_t.assign(c->nbox, 2);
@@ -1283,6 +1468,7 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
                                                 c->prm.n_ngb, c->prm.h_est_mode, c->prm.h_est_factor,
                                                 c->hguess.as<float>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
+    SPH_TRY(build_mark(c, s, 1));
   }
   SPH_TRY(build_from_guess(c, s));
   if (!h_guess && c->prm.h_est_factor != 1.0f) {
@@ -1297,16 +1483,21 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
 int build_from_guess(sph_ctx* c, cudaStream_t s) {
   const long long n = c->n;
   ++c->build_gen;  // device-side graphs hold this decomposition's buffers
+  if (c->profile) ++c->prof_builds;
+  SPH_TRY(build_mark(c, s, -1));
   SPH_TRY(choose_top_levels(c, s));
   SPH_TRY(build_tree(c, 0, s));
   { k_relpos<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), c->xs.as<double>(),
                                           c->d_box_L.as<double>(), c->d_box_t.as<int>(), c->kbits,
                                           c->pos4.as<float4>(), c->p_et.as<float>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
+  SPH_TRY(build_mark(c, s, 2));
   SPH_TRY(build_tasks(c, s));
+  SPH_TRY(build_mark(c, s, 3));
   SPH_TRY(build_blocks_and_sorts(c, s));
   SPH_CUDA(cudaMemcpyAsync(c->h.p, c->hguess.p, sizeof(float) * (size_t)n,
                            cudaMemcpyDeviceToDevice, s));
   SPH_TRY(compute_node_hmax(c, s));
+  SPH_TRY(build_mark(c, s, 7));
   return SPH_OK;
 }

@@ -95,6 +95,7 @@ struct sph_ctx {
   DBuf hlim;      // float per-particle cell limit
   DBuf pnode;     // int leaf node of each particle
   DBuf p_et;      // float top-cell edge of each particle's box
+  DBuf nleaf_dev; // int leaves of the last build
 
   // octree nodes
   int ncell = 0, ntop = 0, max_depth = 0;
@@ -107,6 +108,7 @@ struct sph_ctx {
   DBuf n_hlim;    // float
   DBuf n_sbase;   // long long: base of the node's 13 sorted lists (-1 none)
   DBuf n_nblk, n_blk0;  // leaves: number of particle blocks and the first block
+  DBuf n_listed, n_ex;  // int: node has sorted lists; interaction entries a reference expands to
 
   // tasks
   int nself = 0, npair = 0;
@@ -184,7 +186,13 @@ struct sph_ctx {
   unsigned long long prof_cand_acc[8] = {0};
   double prof_ms[8] = {0};
   int prof_n[8] = {0};
+  double prof_build_ms[8] = {0};
+  int prof_builds = 0;
+  double prof_t = 0;  // host time (ms) of the last build-stage boundary
 };
+// profiling: synchronise the stream and charge the host time since the
+// previous boundary to build stage k (k < 0 only starts the clock)
+int build_mark(sph_ctx* c, cudaStream_t s, int k);
 cudaEvent_t ev_get(sph_ctx* c);
 int prof_resolve(sph_ctx* c);
 

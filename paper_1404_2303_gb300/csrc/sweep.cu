@@ -75,6 +75,7 @@ struct SweepArgs {
   const int* n_count;
   const long long* n_sbase;
   const float* n_hmax;
+  const float* b_hmax;
   const float* s_key;
   const int* s_idx;
   const float4* pos4;   // x_rel, y_rel, z_rel, m
@@ -704,9 +705,16 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           cj = a.dt_cj[e];
           code = a.dt_code[e];
           sh = a.dt_shift[e];
-          ncj = a.n_count[cj];
-          jb = a.n_sbase[cj];
-          if (P::USES_HJ) hj = a.n_hmax[cj];
+          if (cj >= 0) {  // a cell with sorted lists
+            ncj = a.n_count[cj];
+            jb = a.n_sbase[cj];
+            if (P::USES_HJ) hj = a.n_hmax[cj];
+          } else {        // a block of a cell without them
+            const int bj = -1 - cj;
+            ncj = a.b_count[bj];
+            jb = 13ll * a.b_first[bj];
+            if (P::USES_HJ) hj = a.b_hmax[bj];
+          }
         }
         const int dir = code & 255, sgn = (code >> 8) - 1;
         jb += (long long)dir * ncj;
@@ -1065,6 +1073,7 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   a.n_count = c->n_count.as<int>();
   a.n_sbase = c->n_sbase.as<long long>();
   a.n_hmax = c->n_hmax.as<float>();
+  a.b_hmax = c->b_hmax.as<float>();
   a.s_key = c->s_key.as<float>();
   a.s_idx = c->s_idx.as<int>();
   a.pos4 = c->pos4.as<float4>();
