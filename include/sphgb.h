@@ -99,6 +99,10 @@ typedef struct sph_params {
                            read the lists instead of sweeping; a particle with more pairs is
                            swept.  Costs 4 * n * pair_list_cap bytes of device memory; needs
                            sweep_cap <= 256 and n < 2^27; 256 */
+  int32_t list_cap;     /* cells of at most this many particles (0..4096) get their 13 sorted
+                           lists, merged from their children's; a pair task naming a larger
+                           cell walks its listed descendants (or the blocks of a larger leaf)
+                           instead; 4096 */
 } sph_params;
 
 /* Statistics of the last build and sweeps (host copy). */

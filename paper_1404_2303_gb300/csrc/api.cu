@@ -356,6 +356,7 @@ void sph_default_params(sph_params* p) {
   p->use_graph = 1;
   p->sweep_lists = 0x08;
   p->pair_list_cap = 256;
+  p->list_cap = 4096;
 }
 
 int sph_create(const sph_params* p, sph_ctx** out) {
@@ -368,7 +369,8 @@ int sph_create(const sph_params* p, sph_ctx** out) {
       q.morton_bits < 8 || q.morton_bits > 20 || !(q.h_tol > 0.f) || q.warps_per_cta < 1 ||
       q.warps_per_cta > 8 || q.ctas_per_sm < 0 || q.h_est_mode < 0 || q.h_est_mode > 1 ||
       !(q.h_est_factor > 0.f) || q.sweep_cap < 32 || q.sweep_cap > 1024 || (q.sweep_cap % 32) != 0 ||
-      q.sweep_lists < 0 || q.sweep_lists > 0x1f || q.pair_list_cap < 0 || q.pair_list_cap > 4096)
+      q.sweep_lists < 0 || q.sweep_lists > 0x1f || q.pair_list_cap < 0 || q.pair_list_cap > 4096 ||
+      q.list_cap < 0 || q.list_cap > 4096)
     return SPH_ERR_INVALID_ARG;
   sph_ctx* c = new sph_ctx();
   c->prm = q;

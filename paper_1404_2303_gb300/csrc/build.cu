@@ -5,6 +5,7 @@
 // Fig. HierarchySorting) and the per-block interaction lists the sweeps
 // consume.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 
 #include <chrono>
@@ -480,8 +481,8 @@ __global__ void k_need_down(int g0, int g1, const int* child0, int* need) {
 }
 
 // A node is listed (its 13 sorted lists exist) when it holds at most
-// LIST_CAP particles and every descendant is listed; a leaf also needs at
-// most LIST_SUB blocks.  Its lists are then merged in shared memory from its
+// list_cap (<= LIST_CAP) particles and every descendant is listed; a leaf
+// also needs at most LIST_SUB blocks.  Its lists are then merged in shared memory from its
 // children's (or its blocks') lists.  A task that names an unlisted node
 // reaches its particles through the listed descendants, or through the
 // blocks of an unlisted leaf (blocks always have lists).  ex[node] counts the
@@ -490,7 +491,7 @@ constexpr int LIST_CAP = 4096;
 constexpr int LIST_SUB = 16;
 
 __global__ void k_listed(int g0, int g1, const int* child0, const int* count, const int* nblk,
-                         int* listed, int* ex) {
+                         int cap, int* listed, int* ex) {
   int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g1) return;
   const int cnt = count[node];
@@ -501,12 +502,12 @@ __global__ void k_listed(int g0, int g1, const int* child0, const int* count, co
   }
   const int c0 = child0[node];
   if (c0 < 0) {
-    const bool L = cnt <= LIST_CAP && nblk[node] <= LIST_SUB;
+    const bool L = cnt <= cap && nblk[node] <= LIST_SUB;
     listed[node] = L ? 1 : 0;
     ex[node] = L ? 1 : nblk[node];
     return;
   }
-  bool all = cnt <= LIST_CAP;
+  bool all = cnt <= cap;
   int e = 0;
   for (int k = 0; k < 8; ++k) {
     all = all && listed[c0 + k] != 0;
@@ -968,7 +969,86 @@ __global__ void k_internal_hmax(int g0, int g1, const int* child0, float* hmax) 
   hmax[node] = m;
 }
 
+// ---------------------------------------------------------------- bounding boxes
+// of the particles (top-cell frame) of every block and node; empty nodes get
+// an inverted box
+__global__ void k_block_bbox(int nblock, const int* b_first, const int* b_count, const float4* pos4,
+                             float4* lo, float4* hi) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= nblock) return;
+  int f = b_first[warp], c = b_count[warp];
+  float x0 = FLT_MAX, y0 = FLT_MAX, z0 = FLT_MAX, x1 = -FLT_MAX, y1 = -FLT_MAX, z1 = -FLT_MAX;
+  for (int k = lane; k < c; k += 32) {
+    const float4 p = pos4[f + k];
+    x0 = fminf(x0, p.x); y0 = fminf(y0, p.y); z0 = fminf(z0, p.z);
+    x1 = fmaxf(x1, p.x); y1 = fmaxf(y1, p.y); z1 = fmaxf(z1, p.z);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+    y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+    z0 = fminf(z0, __shfl_xor_sync(0xffffffffu, z0, o));
+    x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+    y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    z1 = fmaxf(z1, __shfl_xor_sync(0xffffffffu, z1, o));
+  }
+  if (lane == 0) {
+    lo[warp] = make_float4(x0, y0, z0, 0.f);
+    hi[warp] = make_float4(x1, y1, z1, 0.f);
+  }
+}
+
+__device__ __forceinline__ void box_union(float4& lo, float4& hi, float4 l, float4 h) {
+  lo.x = fminf(lo.x, l.x); lo.y = fminf(lo.y, l.y); lo.z = fminf(lo.z, l.z);
+  hi.x = fmaxf(hi.x, h.x); hi.y = fmaxf(hi.y, h.y); hi.z = fmaxf(hi.z, h.z);
+}
+
+__global__ void k_leaf_bbox(int ncell, const int* child0, const int* nblk, const int* blk0,
+                            const float4* blo, const float4* bhi, float4* lo, float4* hi) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= ncell || child0[id] >= 0) return;
+  float4 l = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.f), h = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.f);
+  for (int k = 0; k < nblk[id]; ++k) box_union(l, h, blo[blk0[id] + k], bhi[blk0[id] + k]);
+  lo[id] = l;
+  hi[id] = h;
+}
+
+__global__ void k_internal_bbox(int g0, int g1, const int* child0, float4* lo, float4* hi) {
+  int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g1) return;
+  int c0 = child0[node];
+  if (c0 < 0) return;
+  float4 l = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.f), h = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.f);
+  for (int k = 0; k < 8; ++k) box_union(l, h, lo[c0 + k], hi[c0 + k]);
+  lo[node] = l;
+  hi[node] = h;
+}
+
 }  // namespace
+
+static int compute_bboxes(sph_ctx* c, cudaStream_t s) {
+  SPH_TRY(dbuf_ensure(c->n_lo, sizeof(float4) * (size_t)(c->ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->n_hi, sizeof(float4) * (size_t)(c->ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->b_lo, sizeof(float4) * (size_t)(c->nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->b_hi, sizeof(float4) * (size_t)(c->nblock + 1)));
+  { k_block_bbox<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, s>>>(
+      c->nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->pos4.as<float4>(),
+      c->b_lo.as<float4>(), c->b_hi.as<float4>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  { k_leaf_bbox<<<div_up(c->ncell, TPB), TPB, 0, s>>>(c->ncell, c->n_child0.as<int>(),
+                                                     c->n_nblk.as<int>(), c->n_blk0.as<int>(),
+                                                     c->b_lo.as<float4>(), c->b_hi.as<float4>(),
+                                                     c->n_lo.as<float4>(), c->n_hi.as<float4>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  for (int g = (int)c->gen_start.size() - 2; g >= 0; --g) {
+    int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
+    if (g1 <= g0) continue;
+    { k_internal_bbox<<<div_up(g1 - g0, TPB), TPB, 0, s>>>(g0, g1, c->n_child0.as<int>(),
+                                                          c->n_lo.as<float4>(), c->n_hi.as<float4>()); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  return SPH_OK;
+}
 
 // ===========================================================================
 // host side
@@ -1279,7 +1359,8 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
     const int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
     if (g1 <= g0) continue;
     { k_listed<<<div_up(g1 - g0, TPB), TPB, 0, s>>>(g0, g1, c->n_child0.as<int>(),
-                                                   c->n_count.as<int>(), nblk, listed, nex); note_launch(); }
+                                                   c->n_count.as<int>(), nblk, c->prm.list_cap,
+                                                   listed, nex); note_launch(); }
     SPH_CUDA(cudaGetLastError());
   }
   // block sorts: lists of all 13 directions at [13 first, 13 (first + count))
@@ -1498,6 +1579,7 @@ int build_from_guess(sph_ctx* c, cudaStream_t s) {
   SPH_CUDA(cudaMemcpyAsync(c->h.p, c->hguess.p, sizeof(float) * (size_t)n,
                            cudaMemcpyDeviceToDevice, s));
   SPH_TRY(compute_node_hmax(c, s));
+  SPH_TRY(compute_bboxes(c, s));
   SPH_TRY(build_mark(c, s, 7));
   return SPH_OK;
 }

@@ -108,6 +108,7 @@ struct sph_ctx {
   DBuf n_hlim;    // float
   DBuf n_sbase;   // long long: base of the node's 13 sorted lists (-1 none)
   DBuf n_nblk, n_blk0;  // leaves: number of particle blocks and the first block
+  DBuf n_lo, n_hi;      // float4 particle bounding box of the node (top-cell frame)
   DBuf n_listed, n_ex;  // int: node has sorted lists; interaction entries a reference expands to
 
   // tasks
@@ -121,6 +122,7 @@ struct sph_ctx {
   int nblock = 0, nleaf = 0;
   int64_t ndt = 0;
   DBuf b_first, b_count, b_leaf, b_dtoff, b_order, b_cost, b_hmax;
+  DBuf b_lo, b_hi;  // float4 particle bounding box of the block
   DBuf dt_cj;      // int
   DBuf dt_code;    // int: dir | (sgn+1) << 8
   DBuf dt_shift;   // float4 (sx, sy, sz, 0)

@@ -76,6 +76,10 @@ struct SweepArgs {
   const long long* n_sbase;
   const float* n_hmax;
   const float* b_hmax;
+  const float4* n_lo;   // particle bounding boxes of cells and blocks
+  const float4* n_hi;
+  const float4* b_lo;
+  const float4* b_hi;
   const float* s_key;
   const int* s_idx;
   const float4* pos4;   // x_rel, y_rel, z_rel, m
@@ -705,16 +709,28 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           cj = a.dt_cj[e];
           code = a.dt_code[e];
           sh = a.dt_shift[e];
+          float4 tlo, thi;
           if (cj >= 0) {  // a cell with sorted lists
             ncj = a.n_count[cj];
             jb = a.n_sbase[cj];
             if (P::USES_HJ) hj = a.n_hmax[cj];
+            tlo = a.n_lo[cj];
+            thi = a.n_hi[cj];
           } else {        // a block of a cell without them
             const int bj = -1 - cj;
             ncj = a.b_count[bj];
             jb = 13ll * a.b_first[bj];
             if (P::USES_HJ) hj = a.b_hmax[bj];
+            tlo = a.b_lo[bj];
+            thi = a.b_hi[bj];
           }
+          // a target whose box lies beyond the reach of the whole chunk has
+          // no candidate (the margin delta covers the rounding of the shift)
+          const float gx = fmaxf(fmaxf(__fadd_rn(tlo.x, sh.x) - bx1, bx0 - __fadd_rn(thi.x, sh.x)), 0.f);
+          const float gy = fmaxf(fmaxf(__fadd_rn(tlo.y, sh.y) - by1, by0 - __fadd_rn(thi.y, sh.y)), 0.f);
+          const float gz = fmaxf(fmaxf(__fadd_rn(tlo.z, sh.z) - bz1, bz0 - __fadd_rn(thi.z, sh.z)), 0.f);
+          const float Ct = (P::USES_HJ ? fmaxf(hmx, hj) : hmx) + a.delta;
+          if (fmaf(gz, gz, fmaf(gy, gy, gx * gx)) > Ct * Ct) ncj = 0;
         }
         const int dir = code & 255, sgn = (code >> 8) - 1;
         jb += (long long)dir * ncj;
@@ -1074,6 +1090,10 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   a.n_sbase = c->n_sbase.as<long long>();
   a.n_hmax = c->n_hmax.as<float>();
   a.b_hmax = c->b_hmax.as<float>();
+  a.n_lo = c->n_lo.as<float4>();
+  a.n_hi = c->n_hi.as<float4>();
+  a.b_lo = c->b_lo.as<float4>();
+  a.b_hi = c->b_hi.as<float4>();
   a.s_key = c->s_key.as<float>();
   a.s_idx = c->s_idx.as<int>();
   a.pos4 = c->pos4.as<float4>();

@@ -196,3 +196,20 @@ def test_autotuner_shapes_do_not_change_results():
         acc = s.force(u)[0].cpu().numpy().astype(np.float64)
         assert np.max(np.abs(rho - ref) / ref) <= 1e-6
         assert _rms_err(acc, acc_ref) <= 1e-5
+
+
+@pytest.mark.parametrize("list_cap", [0, 64])
+@pytest.mark.parametrize("name", ["clumped20k", "multires32"])
+def test_pair_sets_without_cell_lists(name, list_cap, oracle_cache):
+    """Cells above list_cap particles get no sorted lists: tasks reach them
+    through listed descendants or leaf blocks.  The pair sets stay exact."""
+    d, ref = _oracle(name, oracle_cache)
+    n = d["x"].shape[0]
+    h32 = ref["h"].astype(np.float32)
+    s = _sph(list_cap=list_cap)
+    s.build(_t(d["x"]), h_guess=_t(h32))
+    out = s.density_fixed_h(_t(d["m"]), _t(h32), count=True)
+    assert np.array_equal(_pairs_gpu(s, 0, n), O.pairs_fp32(d["x"], h32, "density"))
+    assert np.array_equal(_pairs_gpu(s, 1, n), O.pairs_fp32(d["x"], h32, "force"))
+    den = O.density_at(O.Neighbours(d["x"]), d["m"], h32.astype(np.float64))
+    assert _rel(out["rho"].cpu().numpy().astype(np.float64), den["rho"]) <= RHO_TOL
