@@ -146,25 +146,66 @@ __global__ void k_make_children(int g0, int g1, int next, const int* split, cons
   }
 }
 
-// h estimate from the count-only octree: local number density of the
-// leaf's parent (or of the leaf itself at the top level), turned into the
-// h whose sphere holds N_ngb particles at that density
-__global__ void k_h_estimate(long long n, const int* pnode, const int* parent, const int* count,
-                             const int4* ijk, const int* box, const double* Ls, float n_ngb,
-                             int mode, float factor, float* hout) {
+// h estimate from a count-only octree below a 4^3 top grid whose cells
+// split above EST_SPLIT particles: the local number density of the
+// particle's leaf's parent (or of the leaf itself at the top level; in mode 1
+// the lower of the leaf's and the parent's), turned into the h whose sphere
+// holds N_ngb particles at that density.  The octree is not built: in the
+// sorted Morton keys the particles of the level-L cell holding particle s
+// form one run of equal key prefixes, so the leaf (the first level whose cell
+// holds at most EST_SPLIT particles) and its parent are found by binary
+// searches over the level and over the run ends.
+__device__ __forceinline__ long long first_ge(const unsigned long long* keys, long long a, long long b,
+                                              unsigned long long P, int sh) {
+  while (a < b) {  // first index in [a, b) whose prefix is >= P
+    const long long m = (a + b) >> 1;
+    if ((keys[m] >> sh) < P) a = m + 1; else b = m;
+  }
+  return a;
+}
+__device__ __forceinline__ long long first_gt(const unsigned long long* keys, long long a, long long b,
+                                              unsigned long long P, int sh) {
+  while (a < b) {  // first index in [a, b) whose prefix is > P
+    const long long m = (a + b) >> 1;
+    if ((keys[m] >> sh) <= P) a = m + 1; else b = m;
+  }
+  return a;
+}
+
+__global__ void k_h_estimate_flat(long long n, const unsigned long long* keys, int K, int t0,
+                                  const double* Ls, float n_ngb, int mode, float factor,
+                                  float* hout) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  int node = pnode[s];
-  int par = parent[node];
-  int use = par >= 0 ? par : node;
-  double L = Ls[box[use]];
-  double e = L / (double)(1ll << ijk[use].w);
-  double dens = (double)count[use] / (e * e * e);
-  if (mode == 1 && par >= 0 && count[node] >= 8) {
-    // the lower of the leaf's and its parent's densities: a leaf at the
-    // edge of a clump does not inherit the clump's density
-    double el = L / (double)(1ll << ijk[node].w);
-    dens = fmin(dens, (double)count[node] / (el * el * el));
+  const unsigned long long key = keys[s];
+  const int b = (int)(key >> (3 * K));
+  // run length of s's level-L cell, exact when at most EST_SPLIT (else > EST_SPLIT)
+  auto small_count = [&](int L) -> long long {
+    const int sh = 3 * (K - L);
+    const unsigned long long P = key >> sh;
+    const long long a = s - EST_SPLIT > 0 ? s - EST_SPLIT : 0;
+    const long long e = s + EST_SPLIT + 1 < n ? s + EST_SPLIT + 1 : n;
+    return first_gt(keys, s + 1, e, P, sh) - first_ge(keys, a, s, P, sh);
+  };
+  int lo = t0, hi = K;  // first level whose cell holds <= EST_SPLIT (K at most)
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (small_count(mid) <= EST_SPLIT) hi = mid; else lo = mid + 1;
+  }
+  const int Ll = lo;
+  const double L = Ls[b];
+  const int shl = 3 * (K - Ll);
+  const long long cl = first_gt(keys, s + 1, n, key >> shl, shl) - first_ge(keys, 0, s, key >> shl, shl);
+  const double el = L / (double)(1ll << Ll);
+  double dens;
+  if (Ll > t0) {
+    const int Lp = Ll - 1, shp = 3 * (K - Lp);
+    const long long cp = first_gt(keys, s + 1, n, key >> shp, shp) - first_ge(keys, 0, s, key >> shp, shp);
+    const double ep = L / (double)(1ll << Lp);
+    dens = (double)cp / (ep * ep * ep);
+    if (mode == 1 && cl >= 8) dens = fmin(dens, (double)cl / (el * el * el));
+  } else {
+    dens = (double)cl / (el * el * el);
   }
   double h = (double)factor * cbrt(3.0 * (double)n_ngb / (4.0 * M_PI * dens));
   h = fmin(h, 0.24 * L);
@@ -695,12 +736,12 @@ __global__ void k_block_dts(int nblock, const int* b_leaf, const int* b_count, c
     }
   }
   unsigned cc = c > 4.0e9 ? 0xffffffffu : (unsigned)c;
-  cost[b] = ((unsigned long long)(0xffffffffu - cc) << 32) | (unsigned)b;
+  cost[b] = (unsigned long long)(0xffffffffu - cc);  // ascending key = descending cost
 }
 
-__global__ void k_order_from_keys(int n, const unsigned long long* keys, int* order) {
+__global__ void k_iota(int n, int* v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) order[i] = (int)(keys[i] & 0xffffffffu);
+  if (i < n) v[i] = i;
 }
 
 
@@ -755,19 +796,15 @@ __global__ void k_stats_flat(long long n, const int* pcur, const float* hs, cons
   }
 }
 
-__global__ void k_split_decide(int g0, int g1, int mode, int split_count, float split_frac, int K,
+__global__ void k_split_decide(int g0, int g1, int split_count, float split_frac, int K,
                                const int* count, const int4* ijk, const int* acc_hmax,
                                const int* acc_small, float* hbuild, int* split) {
   int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g1) return;
   int c = count[node];
   hbuild[node] = __int_as_float(acc_hmax[node]);
-  int sp;
-  if (mode == 0)
-    sp = (c > split_count) && ((float)acc_small[node] > split_frac * (float)c) && (ijk[node].w < K);
-  else
-    sp = (c > EST_SPLIT) && (ijk[node].w < K);
-  split[node - g0] = sp;
+  split[node - g0] =
+      (c > split_count) && ((float)acc_small[node] > split_frac * (float)c) && (ijk[node].w < K);
 }
 
 // advance every particle to its child at the next generation (or retire it
@@ -1094,9 +1131,9 @@ static int d2h(T* dst, const void* src, cudaStream_t s) {
   return SPH_OK;
 }
 
-// Octree over the Morton-sorted particles (mode 0: Section 3.2 split rule
-// on the h in c->hguess; mode 1: count-only split for the h estimate).
-static int build_tree(sph_ctx* c, int mode, cudaStream_t s) {
+// Octree over the Morton-sorted particles (Section 3.2 split rule on the h
+// in c->hguess).
+static int build_tree(sph_ctx* c, cudaStream_t s) {
   const int n = (int)c->n;
   const int K = c->kbits;
   // top grid
@@ -1141,9 +1178,9 @@ static int build_tree(sph_ctx* c, int mode, cudaStream_t s) {
     SPH_CUDA(cudaMemsetAsync(acc_s + g0, 0, sizeof(int) * ng, s));
     na = nbufs.arrays();
     { k_stats_flat<<<div_up(n, TPB), TPB, 0, s>>>(n, pcur, c->hguess.as<float>(), na.ijk, na.box,
-                                                 c->d_box_L.as<double>(), mode == 0, acc_h, acc_s); note_launch(); }
+                                                 c->d_box_L.as<double>(), 1, acc_h, acc_s); note_launch(); }
     SPH_CUDA(cudaGetLastError());
-    { k_split_decide<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, mode, c->prm.split_count,
+    { k_split_decide<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, c->prm.split_count,
                                                     c->prm.split_frac, K, na.count, na.ijk, acc_h,
                                                     acc_s, na.hbuild, c->t_cnt.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
@@ -1258,27 +1295,29 @@ static int build_tasks(sph_ctx* c, cudaStream_t s) {
   size_t fs_cap = 0, fp_cap = 0;
   DBuf fs_buf, fp_buf;
   while (nt > 0) {
-    SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * 3 * (size_t)(nt + 1)));
-    SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * 3 * (size_t)(nt + 1)));
+    SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (3 * (size_t)(nt + 1) + 1)));
+    SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (3 * (size_t)(nt + 1) + 1)));
     int* nch = c->t_cnt.as<int>();
     int* nfs = nch + (nt + 1);
     int* nfp = nfs + (nt + 1);
     int* och = c->t_off.as<int>();
     int* ofs = och + (nt + 1);
     int* ofp = ofs + (nt + 1);
+    // the three counts side by side (zero gaps) take one scan: the self and
+    // pair offsets then carry the totals before them
+    SPH_CUDA(cudaMemsetAsync(nch, 0, sizeof(int) * 3 * (size_t)(nt + 1), s));
     { k_refine<<<div_up(nt, TPB), TPB, 0, s>>>(
         nt, c->t_cur.as<int4>(), c->n_child0.as<int>(), c->n_count.as<int>(),
         c->n_hbuild.as<float>(), c->n_ijk.as<int4>(), c->n_box.as<int>(), c->d_box_L.as<double>(),
         nch, nfs, nfp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr); note_launch(); }
     SPH_CUDA(cudaGetLastError());
-    SPH_TRY(scan_exclusive_i32(nch, och, nt, och + nt, c->scan_tmp, s));
-    SPH_TRY(scan_exclusive_i32(nfs, ofs, nt, ofs + nt, c->scan_tmp, s));
-    SPH_TRY(scan_exclusive_i32(nfp, ofp, nt, ofp + nt, c->scan_tmp, s));
-    int tot[3];
-    SPH_CUDA(cudaMemcpyAsync(&tot[0], och + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaMemcpyAsync(&tot[1], ofs + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaMemcpyAsync(&tot[2], ofp + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_TRY(scan_exclusive_i32(nch, och, 3 * (nt + 1), och + 3 * (nt + 1), c->scan_tmp, s));
+    int cum[3];
+    SPH_CUDA(cudaMemcpyAsync(&cum[0], och + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaMemcpyAsync(&cum[1], ofs + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaMemcpyAsync(&cum[2], ofp + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
     SPH_CUDA(cudaStreamSynchronize(s));
+    const int tot[3] = {cum[0], cum[1] - cum[0], cum[2] - cum[1]};
     SPH_TRY(dbuf_ensure(c->t_next, sizeof(int4) * (size_t)(tot[0] + 1)));
     if ((size_t)(nfs_total + tot[1]) > fs_cap) {
       fs_cap = (size_t)(nfs_total + tot[1]) * 2 + 1024;
@@ -1292,7 +1331,7 @@ static int build_tasks(sph_ctx* c, cudaStream_t s) {
         nt, c->t_cur.as<int4>(), c->n_child0.as<int>(), c->n_count.as<int>(),
         c->n_hbuild.as<float>(), c->n_ijk.as<int4>(), c->n_box.as<int>(), c->d_box_L.as<double>(),
         nullptr, nullptr, nullptr, och, ofs, ofp, c->t_next.as<int4>(), fs_buf.as<int>(),
-        fp_buf.as<int4>(), nfs_total, nfp_total, c->n_flags.as<int>()); note_launch(); }
+        fp_buf.as<int4>(), nfs_total - cum[0], nfp_total - cum[1], c->n_flags.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
     nfs_total += tot[1];
     nfp_total += tot[2];
@@ -1484,13 +1523,11 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
       listed, c->n_child0.as<int>(), nblk, blk0, c->b_dtoff.as<long long>(), c->dt_cj.as<int>(),
       c->dt_code.as<int>(), c->dt_shift.as<float4>(), ck); note_launch(); }
   SPH_CUDA(cudaGetLastError());
-  // LPT order: descending cost, ties by block id
+  // LPT order: descending cost, ties by block id (the sort is stable)
   int* ov = c->b_order.as<int>();
-  { k_order_from_keys<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, ck, ov); note_launch(); }
+  { k_iota<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, ov); note_launch(); }
   SPH_CUDA(cudaGetLastError());
-  SPH_TRY(radix_sort_u64(ck, ov, ck + (nblock + 1), ov + (nblock + 1), nblock, 64, c->sort_tmp, s));
-  { k_order_from_keys<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, ck, ov); note_launch(); }
-  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(radix_sort_u64(ck, ov, ck + (nblock + 1), ov + (nblock + 1), nblock, 32, c->sort_tmp, s));
   // leaves (nodes with blocks), counted on the device; read with the statistics
   SPH_TRY(dbuf_ensure(c->nleaf_dev, 64));
   SPH_CUDA(cudaMemsetAsync(c->nleaf_dev.p, 0, sizeof(int), s));
@@ -1540,14 +1577,13 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
   SPH_CUDA(cudaGetLastError());
   SPH_TRY(build_mark(c, s, 0));
   if (!h_guess) {
-    // count-only octree below a 4^3 top grid gives a local-density h estimate
-    c->box_t.assign(c->nbox, 2);
-    SPH_TRY(build_tree(c, 1, s));
-    { k_h_estimate<<<div_up(n, TPB), TPB, 0, s>>>(n, c->pnode.as<int>(), c->n_parent.as<int>(),
-                                                c->n_count.as<int>(), c->n_ijk.as<int4>(),
-                                                c->n_box.as<int>(), c->d_box_L.as<double>(),
-                                                c->prm.n_ngb, c->prm.h_est_mode, c->prm.h_est_factor,
-                                                c->hguess.as<float>()); note_launch(); }
+    // the count-only octree below a 4^3 top grid (cells split above
+    // EST_SPLIT particles) gives a local-density h estimate, read off the
+    // sorted keys without building that octree
+    { k_h_estimate_flat<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), K, 2,
+                                                     c->d_box_L.as<double>(), c->prm.n_ngb,
+                                                     c->prm.h_est_mode, c->prm.h_est_factor,
+                                                     c->hguess.as<float>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
     SPH_TRY(build_mark(c, s, 1));
   }
@@ -1567,7 +1603,7 @@ int build_from_guess(sph_ctx* c, cudaStream_t s) {
   if (c->profile) ++c->prof_builds;
   SPH_TRY(build_mark(c, s, -1));
   SPH_TRY(choose_top_levels(c, s));
-  SPH_TRY(build_tree(c, 0, s));
+  SPH_TRY(build_tree(c, s));
   { k_relpos<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), c->xs.as<double>(),
                                           c->d_box_L.as<double>(), c->d_box_t.as<int>(), c->kbits,
                                           c->pos4.as<float4>(), c->p_et.as<float>()); note_launch(); }
