@@ -63,8 +63,9 @@ __global__ void k_hsolve_init(long long n, float* h, const float* hlim, double* 
 }
 
 __global__ void k_hsolve_update(long long n, float* h, const float* hlim, const float* nngb,
-                                const float* dnngb, double* lo, double* hi, float* dxold, int* flag,
-                                float n_ngb, float tol, int* nactive, int* nlimit) {
+                                const float* dnngb, const float* d2nngb, double* lo, double* hi,
+                                float* dxold, int* flag, float n_ngb, float tol, int* nactive,
+                                int* nlimit) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int fl = flag[s];
@@ -89,10 +90,18 @@ __global__ void k_hsolve_update(long long n, float* h, const float* hlim, const 
     H = hd;
     fl |= HF_HI_VALID;
   }
-  // Newton step in x = ln h on g(x) = ln N - ln n_ngb, g'(x) = h N'/N
+  // Halley step in x = ln h on g(x) = ln N - ln n_ngb, with g'(x) = h N'/N
+  // and g''(x) = g' + h^2 N''/N - g'^2 (cubic convergence near the root;
+  // the Newton step g/g' where the correction is not well conditioned)
   const float slope = (dnngb[s] > 0.f && Nv > 0.f) ? (float)(hd * (double)dnngb[s] / (double)Nv) : 0.f;
   const float g = __logf(Nv) - __logf(n_ngb);
-  const float dx = slope > 1e-3f ? g / slope : 0.f;  // ln(h / h_new)
+  float dx = slope > 1e-3f ? g / slope : 0.f;  // ln(h / h_new)
+  if (slope > 1e-3f) {
+    const float hf0 = (float)hd;
+    const float curv = slope + hf0 * hf0 * d2nngb[s] / Nv - slope * slope;
+    const float den = 2.f * slope * slope - g * curv;
+    if (den > slope * slope) dx = 2.f * g * slope / den;
+  }
   double hn;
   float step;
   if (fl & HF_HI_VALID) {
@@ -242,7 +251,7 @@ static int read_status(sph_ctx* c, cudaStream_t s) {
 
 static int ensure_state(sph_ctx* c) {
   const size_t n = (size_t)c->n;
-  DBuf* f1[] = {&c->rho, &c->drho, &c->nngb, &c->dnngb, &c->d2rho, &c->omega, &c->Avec, &c->u_s};
+  DBuf* f1[] = {&c->rho, &c->drho, &c->nngb, &c->dnngb, &c->d2nngb, &c->d2rho, &c->omega, &c->Avec, &c->u_s};
   for (DBuf* b : f1) SPH_TRY(dbuf_ensure(*b, 4 * n));
   SPH_TRY(dbuf_ensure(c->fdat, 16 * n));
   SPH_TRY(dbuf_ensure(c->vel4, 16 * n));
@@ -308,8 +317,8 @@ static int solve_round_graph(sph_ctx* c, cudaStream_t s, int* host, int* iters) 
     if (r == SPH_OK && cudaMemsetAsync(ctl, 0, sizeof(int), cs) != cudaSuccess) r = SPH_ERR_CUDA;
     { k_hsolve_update<<<div_up(n, TPB), TPB, 0, cs>>>(
         n, c->h.as<float>(), c->hlim.as<float>(), c->nngb.as<float>(), c->dnngb.as<float>(),
-        c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_dx.as<float>(), c->h_flag.as<int>(),
-        c->prm.n_ngb, c->prm.h_tol, ctl, ctl + 1); note_launch(); }
+        c->d2nngb.as<float>(), c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_dx.as<float>(),
+        c->h_flag.as<int>(), c->prm.n_ngb, c->prm.h_tol, ctl, ctl + 1); note_launch(); }
     { k_loop_ctl<<<1, 1, 0, cs>>>(ctl, ctl + 2, ctl + 3, c->prm.max_newton, hnd); note_launch(); }
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &captured);
@@ -404,7 +413,7 @@ void sph_destroy(sph_ctx* c) {
                  &c->t_cnt2, &c->t_off, &c->t_off2, &c->b_first, &c->b_count, &c->b_leaf,
                  &c->b_dtoff, &c->b_order, &c->b_cost, &c->dt_cj, &c->dt_code, &c->dt_shift,
                  &c->adj_off, &c->adj_list, &c->s_key, &c->s_idx, &c->rho, &c->drho, &c->nngb,
-                 &c->dnngb, &c->d2rho, &c->omega, &c->Avec, &c->fdat, &c->vel4, &c->u_s, &c->acc4,
+                 &c->dnngb, &c->d2nngb, &c->d2rho, &c->omega, &c->Avec, &c->fdat, &c->vel4, &c->u_s, &c->acc4,
                  &c->cnt_i, &c->h_lo, &c->h_hi, &c->h_dx, &c->h_flag, &c->blk_active, &c->adj4, &c->adj4b, &c->g_A,
                  &c->g_rho_s, &c->g_drho_s, &c->g_h_s, &c->g_u_s, &c->g_x4,
                  &c->prof_units, &c->solve_ctl, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
@@ -536,8 +545,8 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
       SPH_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), s));
       { k_hsolve_update<<<div_up(n, TPB), TPB, 0, s>>>(
           n, c->h.as<float>(), c->hlim.as<float>(), c->nngb.as<float>(), c->dnngb.as<float>(),
-          c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_dx.as<float>(), c->h_flag.as<int>(),
-          c->prm.n_ngb, c->prm.h_tol, nact, nlim); note_launch(); }
+          c->d2nngb.as<float>(), c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_dx.as<float>(),
+          c->h_flag.as<int>(), c->prm.n_ngb, c->prm.h_tol, nact, nlim); note_launch(); }
       SPH_CUDA(cudaGetLastError());
       SPH_CUDA(cudaMemcpyAsync(host, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       SPH_CUDA(cudaStreamSynchronize(s));

@@ -134,6 +134,7 @@ struct sph_ctx {
 
   // physics state (cell order)
   DBuf rho, drho, nngb, dnngb, d2rho, omega, Avec, fdat;  // fdat: float4 per particle for force
+  DBuf d2nngb;    // float d^2 N / dh^2 (h iteration)
   DBuf vel4;      // float4 (vx, vy, vz, hinv)
   DBuf u_s;       // float
   DBuf acc4;      // float4 (ax, ay, az, dudt)

@@ -100,6 +100,7 @@ struct SweepArgs {
   float* o1;
   float* o2;
   float* o3;
+  float* o6;
   float4* o4;
   float4* o5;
   int* ocnt;
@@ -124,11 +125,13 @@ struct SweepArgs {
 
 // ---------------------------------------------------------------------------
 // density, Eq. (rho) and Eq. (nneigh): per directed interaction (i <- j),
-// with w = 2 (a^3 - 4 b^3), w' = 6 (4 b^2 - a^2), a = (1-q)+, b = (1/2-q)+,
-// accumulate  m w/2,  m (w/2 + q w'/6),  w/2,  q w'/6
+// with w = 2 (a^3 - 4 b^3), w' = 6 (4 b^2 - a^2), w'' = 12 (a - 4 b),
+// a = (1-q)+, b = (1/2-q)+, accumulate  m w/2,  m (w/2 + q w'/6),  w/2,
+// q w'/6  and  q (q w''/12 + w'/6)  (the last for d^2 N/dh^2, which the h
+// iteration's Halley step uses)
 // ---------------------------------------------------------------------------
 struct PDensity {
-  static constexpr int NACC = 4;
+  static constexpr int NACC = 5;
   static constexpr int JW = 1;
   static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = false;
@@ -173,9 +176,11 @@ struct PDensity {
     acc[1] = fmaf(p.w, wh + qd, acc[1]);
     acc[2] += wh;
     acc[3] += qd;
+    acc[4] = fmaf(q, fmaf(q, fmaf(-4.f, bb, aa), d6), acc[4]);
     if (COUNT) cnt += r2 < i.h2 ? 1 : 0;
   }
-  // rho = sigma/h^3 * 2 S0; drho/dh = -sigma/h^4 * 6 S1; N = 64/3 S2; dN/dh = -64/h S3
+  // rho = sigma/h^3 * 2 S0; drho/dh = -sigma/h^4 * 6 S1; N = 64/3 S2; dN/dh = -64/h S3;
+  // d^2N/dh^2 = 128/h^2 S4
   __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
     float h = a.h[p];
     float hi = 1.0f / h;
@@ -184,6 +189,7 @@ struct PDensity {
     if (a.o1) a.o1[p] = -6.f * SIGMA * hi3 * hi * s[1];
     if (a.o2) a.o2[p] = (64.f / 3.f) * s[2];
     if (a.o3) a.o3[p] = -64.f * hi * s[3];
+    if (a.o6) a.o6[p] = 128.f * hi * hi * s[4];
   }
 };
 
@@ -896,17 +902,15 @@ int launch_shape(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
 // a phase over the force pairs (or a subset of them) from the recorded pair
 // lists: one lane per particle, 32 consecutive particles per warp, each
 // lane walks its own list (coalesced: entry k of the warp's 32 particles is
-// one 128-byte row), stages its j in its own shared-memory slot and applies
-// the phase's predicate and interaction; particles whose list overflowed
-// are left to a masked sweep
+// one 128-byte row), gathers its j data into registers and applies the
+// phase's predicate and interaction; particles whose list overflowed are
+// left to a masked sweep
 // ---------------------------------------------------------------------------
 constexpr int LE_WARPS = 8;
 
 template <class P, bool COUNT>
 __global__ void __launch_bounds__(LE_WARPS * 32) k_listeval(SweepArgs a) {
-  __shared__ float4 tiles[LE_WARPS][P::JW * 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4* tile = tiles[warp];
   const long long ngrp = (a.n + 31) >> 5;
   for (long long g = (long long)blockIdx.x * LE_WARPS + warp; g < ngrp;
        g += (long long)gridDim.x * LE_WARPS) {
@@ -922,20 +926,33 @@ __global__ void __launch_bounds__(LE_WARPS * 32) k_listeval(SweepArgs a) {
     int cnt = 0;
     const int nmax = __reduce_max_sync(FULL, vi ? np : 0);
     const unsigned* wl = a.fl_list + ((size_t)g * a.fl_K) * 32 + lane;
+    // UNR entries per step, their loads issued before any arithmetic; the j
+    // data of an entry sit in registers (a one-slot tile)
+    constexpr int UNR = P::JW >= 3 ? 2 : 4;
+    constexpr unsigned NONE = 0xffffffffu;  // image code 31: no entry
     for (int k0 = 0; k0 < nmax; k0 += 32) {
       const int k1 = min(nmax, k0 + 32);
-      for (int k = k0; k < k1; ++k) {
-        if (k < np) {
-          const unsigned e = wl[(size_t)k * 32];
-          const int j = (int)(e & TAG_J);
-          const int im = (int)(e >> 27);
-          const float4 q = a.pos4[j];
-          const float4 pj = make_float4(__fadd_rn(q.x, (float)(im / 9 - 1) * et),
-                                        __fadd_rn(q.y, (float)((im / 3) % 3 - 1) * et),
-                                        __fadd_rn(q.z, (float)(im % 3 - 1) * et), q.w);
-          P::stage(a, j, e, pj, tile, lane, 32);
-          if (P::test(I, tile, lane, 32)) P::template interact<COUNT>(I, tile, lane, part, cnt, 32);
+      for (int k = k0; k < k1; k += UNR) {
+        unsigned e[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) e[u] = k + u < np ? wl[(size_t)(k + u) * 32] : NONE;
+        float4 tl[UNR][P::JW];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          if (e[u] != NONE) {
+            const int j = (int)(e[u] & TAG_J);
+            const int im = (int)(e[u] >> 27);
+            const float4 q = a.pos4[j];
+            const float4 pj = make_float4(__fadd_rn(q.x, (float)(im / 9 - 1) * et),
+                                          __fadd_rn(q.y, (float)((im / 3) % 3 - 1) * et),
+                                          __fadd_rn(q.z, (float)(im % 3 - 1) * et), q.w);
+            P::stage(a, j, e[u], pj, tl[u], 0, 1);
+          }
         }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+          if (e[u] != NONE && P::test(I, tl[u], 0, 1))
+            P::template interact<COUNT>(I, tl[u], 0, part, cnt, 1);
       }
       fold<P>(acc, cmp, part, a.kahan);
     }
@@ -1115,6 +1132,7 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
       a.o1 = c->drho.as<float>();
       a.o2 = c->nngb.as<float>();
       a.o3 = c->dnngb.as<float>();
+      a.o6 = c->d2nngb.as<float>();
       return counting ? launch<PDensity, true>(c, a, s) : launch<PDensity, false>(c, a, s);
     case PH_DENSITY_D2:
       a.o0 = c->d2rho.as<float>();
