@@ -36,6 +36,14 @@ UNIT = "interactions/s"
 # counted once (the first and third as fixed for this path; the others
 # derived the same way from the minimal arithmetic of each pair term)
 INSTR = {0: 18.0, 1: 24.0, 2: 40.0, 3: 100.0, 4: 65.0}
+# the kernels behind each phase: the density and force phases sweep the
+# sorted cell pairs (the force sweep also records the pair lists); the later
+# phases over the force pairs read those lists (a masked sweep takes the
+# particles whose list overflowed)
+PHASE_KERNELS = {0: "k_sweep<PDensity>", 1: "k_listeval<PDensityD2>", 2: "k_sweep<PForce>",
+                 3: "k_listeval<PForceAdj>", 4: "k_listeval<PDensityAdj>"}
+BUILD_STAGES = ["morton_order", "h_estimate", "octree", "pair_tasks", "blocks_and_block_sorts",
+                "list_merge", "interaction_lists", "node_h_max"]
 PHASE_NAMES = {0: "density", 1: "density_d2", 2: "force", 3: "force_adjoint", 4: "density_adjoint"}
 SMS = 152
 LANES = 128
@@ -211,6 +219,8 @@ def main():
     ap.add_argument("--block-max", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the naive-versus-sorted sweep comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -364,6 +374,7 @@ def main():
         if ph >= 2:
             u_ph = u_ph / 2.0  # ordered -> unordered pairs
         kernels[PHASE_NAMES[ph]] = {
+            "kernel": PHASE_KERNELS[ph],
             "launches_per_step": L / args.steps, "ms_per_launch": phase_ms[ph] / L,
             "units_per_launch": u_ph / L,
             "share_of_step": phase_ms[ph] / args.steps / prof["ms"],
@@ -373,12 +384,41 @@ def main():
     if dom in INSTR and st["sweep_launches"][dom] > 0:
         k = kernels[dname]
         achieved = k["units_per_launch"] * INSTR[dom] / (k["ms_per_launch"] / 1e3)
-        roof = {"kernel": f"k_sweep<{dname}>", "bound": "alu", "achieved": achieved / 1e12,
+        roof = {"kernel": PHASE_KERNELS[dom], "bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak_alu / 1e12, "unit": "T FP32-instr/s",
                 "frac": achieved / peak_alu, "traffic": profiled_traffic(dname),
                 "peak_source": f"{SMS} SMs x {LANES} FP32 lanes x {sm_max:.0f} MHz "
                                f"(sm_max_mhz of {pk_kind} peaks)",
                 "instr_per_unit": INSTR[dom]}
+    # ---- ablation of the sorting (Section 3.3): the naive cell-pair loop over
+    # the same tasks, one density and one force sweep at the solved h each
+    ablation = None
+    if not args.no_ablation:
+        ablation = {}
+        h_sol = den["h"]
+        for mode, name in ((1, "sorted"), (0, "naive")):
+            sa = SPH(sorted_sweep=mode, pair_list_cap=0, **params)
+            if batched:
+                sa.build_batch(pos, d["offsets"], d["boxes"], h_guess=h_sol)
+            else:
+                sa.build(pos, h_guess=h_sol)
+            sa.density_fixed_h(m, h_sol)
+            sa.force(u, vel)
+            torch.cuda.synchronize()
+            sa.profile(True)
+            for _ in range(3):
+                sa.density_fixed_h(m, h_sol)
+                sa.force(u, vel)
+            torch.cuda.synchronize()
+            sst = sa.stats()
+            sa.profile(False)
+            ablation[name] = {
+                "density_ms": sst["sweep_ms"][0] / 3, "force_ms": sst["sweep_ms"][2] / 3,
+                "density_accepted_fraction": sst["sweep_units"][0] / max(1, sst["sweep_candidates"][0]),
+                "force_accepted_fraction": sst["sweep_units"][2] / max(1, sst["sweep_candidates"][2])}
+            sa.close()
+        ablation["sorting_speedup"] = {
+            k: ablation["naive"][k] / ablation["sorted"][k] for k in ("density_ms", "force_ms")}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -418,6 +458,9 @@ def main():
             "decomposition": {k: prod["stats"][k] for k in ("ncell", "nleaf", "nblock", "nself", "npair",
                                                             "ndt", "max_depth", "newton_iters",
                                                             "rebuilds")},
+            "h_iteration_active": [x for x in prod["stats"]["newton_active"] if x],
+            "ablation_naive_vs_sorted": ablation,
+            "build_stages_ms": {BUILD_STAGES[k]: st["build_ms"][k] / args.steps for k in range(8)},
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

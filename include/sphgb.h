@@ -103,6 +103,10 @@ typedef struct sph_params {
                            lists, merged from their children's; a pair task naming a larger
                            cell walks its listed descendants (or the blocks of a larger leaf)
                            instead; 4096 */
+  int32_t sorted_sweep; /* 1: sorted cell-pair sweeps (Section 3.3: axial windows in the
+                           sorted lists, candidates filtered by the chunk's box); 0: the
+                           naive cell-pair loop over the same tasks, every particle of every
+                           target a candidate (ablation of the sorting; same results); 1 */
 } sph_params;
 
 /* Statistics of the last build and sweeps (host copy). */

@@ -29,6 +29,7 @@ class SphParams(C.Structure):
         ("h_est_mode", C.c_int32), ("h_est_factor", C.c_float), ("sweep_cap", C.c_int32),
         ("use_graph", C.c_int32), ("sweep_lists", C.c_int32),
         ("pair_list_cap", C.c_int32), ("list_cap", C.c_int32),
+        ("sorted_sweep", C.c_int32),
     ]
 
 

@@ -366,6 +366,7 @@ void sph_default_params(sph_params* p) {
   p->sweep_lists = 0x08;
   p->pair_list_cap = 256;
   p->list_cap = 4096;
+  p->sorted_sweep = 1;
 }
 
 int sph_create(const sph_params* p, sph_ctx** out) {
@@ -379,7 +380,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
       q.warps_per_cta > 8 || q.ctas_per_sm < 0 || q.h_est_mode < 0 || q.h_est_mode > 1 ||
       !(q.h_est_factor > 0.f) || q.sweep_cap < 32 || q.sweep_cap > 1024 || (q.sweep_cap % 32) != 0 ||
       q.sweep_lists < 0 || q.sweep_lists > 0x1f || q.pair_list_cap < 0 || q.pair_list_cap > 4096 ||
-      q.list_cap < 0 || q.list_cap > 4096)
+      q.list_cap < 0 || q.list_cap > 4096 || q.sorted_sweep < 0 || q.sorted_sweep > 1)
     return SPH_ERR_INVALID_ARG;
   sph_ctx* c = new sph_ctx();
   c->prm = q;

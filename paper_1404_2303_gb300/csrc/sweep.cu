@@ -93,6 +93,7 @@ struct SweepArgs {
   int* status;
   float delta;
   int kahan;
+  int naive;            // ablation: whole targets, no axial window, no box filter
   int bmax;             // largest block (particles)
   const int* pflag;     // h iteration: per-particle flags (bit 0: still iterating)
   // outputs (cell order)
@@ -736,7 +737,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           const float gy = fmaxf(fmaxf(__fadd_rn(tlo.y, sh.y) - by1, by0 - __fadd_rn(thi.y, sh.y)), 0.f);
           const float gz = fmaxf(fmaxf(__fadd_rn(tlo.z, sh.z) - bz1, bz0 - __fadd_rn(thi.z, sh.z)), 0.f);
           const float Ct = (P::USES_HJ ? fmaxf(hmx, hj) : hmx) + a.delta;
-          if (fmaf(gz, gz, fmaf(gy, gy, gx * gx)) > Ct * Ct) ncj = 0;
+          if (!a.naive && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) > Ct * Ct) ncj = 0;
         }
         const int dir = code & 255, sgn = (code >> 8) - 1;
         jb += (long long)dir * ncj;
@@ -752,7 +753,9 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           L = fminf(L, k - ct);
         }
         int js = 0, jn = 0;
-        if (ve && ncj > 0) {
+        if (a.naive) {
+          jn = ve ? ncj : 0;  // every particle of the target is a candidate
+        } else if (ve && ncj > 0) {
           const float* K = a.s_key + jb;
           if (sgn > 0) {
             SPH_PARTITION(ncj, K[mid] + ksh <= U, jn);
@@ -807,7 +810,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
               const float cj = fmaxf(hmx, a.h[jidx]) + a.delta;
               lim2 = cj * cj;
             }
-            take = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= lim2;
+            take = a.naive || fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= lim2;
           }
           const unsigned mt = __ballot_sync(FULL, take);
           const int nt = __popc(mt);
@@ -1125,6 +1128,7 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   for (int b = 0; b < c->nbox; ++b) emax = std::max(emax, c->box_L[b] / (double)(1 << c->box_t[b]));
   a.delta = (float)(emax * (1.0 / 65536.0));
   a.kahan = c->prm.kahan ? 1 : 0;
+  a.naive = c->prm.sorted_sweep ? 0 : 1;
   a.ocnt = counting ? c->cnt_i.as<int>() : nullptr;
   switch (phase) {
     case PH_DENSITY:

@@ -213,3 +213,27 @@ def test_pair_sets_without_cell_lists(name, list_cap, oracle_cache):
     assert np.array_equal(_pairs_gpu(s, 1, n), O.pairs_fp32(d["x"], h32, "force"))
     den = O.density_at(O.Neighbours(d["x"]), d["m"], h32.astype(np.float64))
     assert _rel(out["rho"].cpu().numpy().astype(np.float64), den["rho"]) <= RHO_TOL
+
+
+def test_naive_cell_pair_loop_matches_sorted_sweep(oracle_cache):
+    """Ablation of the sorting (the paper's naive cell-pair loop over the
+    same tasks): identical pair sets, the same sums to FP32 rounding, and
+    far more candidates."""
+    d, ref = _oracle("clumped20k", oracle_cache)
+    n = d["x"].shape[0]
+    h32 = ref["h"].astype(np.float32)
+    out = {}
+    for mode in (1, 0):
+        s = _sph(sorted_sweep=mode)
+        s.build(_t(d["x"]), h_guess=_t(h32))
+        s.profile(True)
+        rho = s.density_fixed_h(_t(d["m"]), _t(h32), count=True)["rho"].cpu().numpy()
+        st = s.stats()
+        s.profile(False)
+        out[mode] = (rho.astype(np.float64), _pairs_gpu(s, 0, n), _pairs_gpu(s, 1, n),
+                     st["sweep_units"][0], st["sweep_candidates"][0])
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+    assert np.array_equal(out[1][1], O.pairs_fp32(d["x"], h32, "density"))
+    assert np.max(np.abs(out[0][0] - out[1][0]) / out[1][0]) <= 1e-6
+    assert out[0][3] == out[1][3]
+    assert out[0][4] > 2 * out[1][4]
