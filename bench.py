@@ -221,6 +221,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the naive-versus-sorted sweep comparison")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="for kernel profilers: run --warmup steps, then one step with the h "
+                         "iteration as a host loop (every sweep a separate launch), and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -251,6 +254,19 @@ def main():
         params["block_max"] = args.block_max
     if args.warps:
         params["warps_per_cta"] = args.warps
+    if args.profile_step:
+        sp = SPH(use_graph=0, **params)
+        for _ in range(args.warmup + 1):
+            if "offsets" in d:
+                sp.build_batch(pos, d["offsets"], d["boxes"])
+            else:
+                sp.build(pos)
+            den = sp.density(m)
+            acc, _, _ = sp.force(u, vel)
+            sp.adjoint(2.0 * (den["rho"] - 1.0), 2.0 * acc, None)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": args.workload, "iters": den["iters"]}), flush=True)
+        return 0
     sph = SPH(**params)
     stream = torch.cuda.current_stream()
     batched = "offsets" in d
