@@ -418,7 +418,9 @@ void sph_destroy(sph_ctx* c) {
                  &c->cnt_i, &c->h_lo, &c->h_hi, &c->h_dx, &c->h_flag, &c->blk_active, &c->adj4, &c->adj4b, &c->g_A,
                  &c->g_rho_s, &c->g_drho_s, &c->g_h_s, &c->g_u_s, &c->g_x4,
                  &c->prof_units, &c->solve_ctl, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
-                 &c->tmp_b, &c->tmp_c};
+                 &c->tmp_b, &c->tmp_c, &c->p_et, &c->nleaf_dev, &c->n_listed, &c->n_ex, &c->n_lo,
+                 &c->n_hi, &c->b_lo, &c->b_hi, &c->fl_list, &c->fl_cnt, &c->fl_flag, &c->fl_blk,
+                 &c->fl_over, &c->task_ctl};
   for (DBuf* b : all) dbuf_free(*b);
   for (auto& e : c->ev_pending) {
     cudaEventDestroy(e.a);

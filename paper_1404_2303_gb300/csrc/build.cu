@@ -281,14 +281,20 @@ __device__ __forceinline__ bool pair_splits(int a, int b, const int* child0, con
 }
 
 // count (out == nullptr) or emit the children of each task; final tasks go
-// to the self / pair lists
-__global__ void k_refine(int nt, const int4* tasks, const int* child0, const int* count,
-                         const float* hb, const int4* ijk, const int* box, const double* Ls,
-                         int* nchild, int* nfs, int* nfp, const int* off_c, const int* off_s,
-                         const int* off_p, int4* out, int* fin_self, int4* fin_pair, int fs_base,
-                         int fp_base, int* psplit) {
+// to the self / pair lists.  The task count *ntp and the list lengths so far
+// (fin_len: self, pair) live on the device.  In emit mode the offsets come
+// from one exclusive scan over [child counts | self counts | pair counts]
+// (each cap + 1 long, zero gaps), so the self and pair offsets carry the
+// totals before them (off_s[cap], off_p[cap] hold the running sums).
+__global__ void k_refine(const int* ntp, int cap, const int4* tasks, const int* child0,
+                         const int* count, const float* hb, const int4* ijk, const int* box,
+                         const double* Ls, int* nchild, int* nfs, int* nfp, const int* off_c,
+                         const int* off_s, const int* off_p, int4* out, int* fin_self,
+                         int4* fin_pair, const int* fin_len, int* psplit) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
+  if (t >= *ntp || t >= cap) return;
+  const int fs_base = out ? fin_len[0] - off_c[cap] : 0;
+  const int fp_base = out ? fin_len[1] - off_s[cap] : 0;
   int4 tk = tasks[t];
   int nc = 0, fs = 0, fp = 0;
   int oc = off_c ? off_c[t] : 0;
@@ -349,6 +355,15 @@ __global__ void k_refine(int nt, const int4* tasks, const int* child0, const int
     nfs[t] = fs;
     nfp[t] = fp;
   }
+}
+
+// after an emit pass: the next generation's task count and the list lengths
+__global__ void k_refine_advance(int cap, const int* off_c, const int* off_s, const int* off_p,
+                                 int* ntp, int* fin_len) {
+  const int tch = off_c[cap], tcs = off_s[cap], tcp = off_p[cap];
+  *ntp = tch;
+  fin_len[0] += tcs - tch;
+  fin_len[1] += tcp - tcs;
 }
 
 __global__ void k_hlim(int g0, int g1, const int* parent, const int* psplit, const int4* ijk,
@@ -1272,10 +1287,26 @@ static int build_tasks(sph_ctx* c, cudaStream_t s) {
   // psplit flags (n_flags) cleared
   SPH_TRY(dbuf_ensure(c->n_flags, sizeof(int) * ncell));
   SPH_CUDA(cudaMemsetAsync(c->n_flags.p, 0, sizeof(int) * ncell, s));
-  // generation 0: top cells
-  int ntop = c->ntop;
-  SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (ntop + 1)));
-  SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (ntop + 1)));
+  // Tasks of generation g join cells of octree generation g: at most one
+  // self task and 13 pair tasks per cell (26 neighbours, each pair once), so
+  // every buffer is sized from the octree and the generations run without a
+  // host round trip; one read of the list lengths at the end.
+  const int ngen = (int)c->gen_start.size() - 1;
+  size_t capmax = 1;
+  for (int g = 0; g < ngen; ++g)
+    capmax = std::max(capmax, (size_t)14 * (size_t)(c->gen_start[g + 1] - c->gen_start[g]));
+  SPH_TRY(dbuf_ensure(c->t_cur, sizeof(int4) * (capmax + 1)));
+  SPH_TRY(dbuf_ensure(c->t_next, sizeof(int4) * (capmax + 1)));
+  SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (3 * (capmax + 1) + 1)));
+  SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (3 * (capmax + 1) + 1)));
+  SPH_TRY(dbuf_ensure(c->t_final_self, sizeof(int) * ((size_t)ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->t_final_pair, sizeof(int4) * (13 * (size_t)ncell + 1)));
+  SPH_TRY(dbuf_ensure(c->task_ctl, 64));
+  int* ntp = c->task_ctl.as<int>();
+  int* fin_len = ntp + 1;
+  // generation 0: the top cells' self tasks and their pairs with the 13
+  // half-neighbour top cells
+  const int ntop = c->ntop;
   { k_top_tasks<<<div_up(ntop, TPB), TPB, 0, s>>>(ntop, c->d_top_base.as<int>(),
                                                 c->d_box_t.as<int>(), c->nbox,
                                                 c->n_count.as<int>(), nullptr,
@@ -1283,67 +1314,45 @@ static int build_tasks(sph_ctx* c, cudaStream_t s) {
   SPH_CUDA(cudaGetLastError());
   SPH_TRY(scan_exclusive_i32(c->t_cnt.as<int>(), c->t_off.as<int>(), ntop,
                              c->t_off.as<int>() + ntop, c->scan_tmp, s));
-  int nt = 0;
-  SPH_TRY(d2h(&nt, c->t_off.as<int>() + ntop, s));
-  SPH_TRY(dbuf_ensure(c->t_cur, sizeof(int4) * (size_t)(nt + 1)));
   { k_top_tasks<<<div_up(ntop, TPB), TPB, 0, s>>>(ntop, c->d_top_base.as<int>(),
                                                 c->d_box_t.as<int>(), c->nbox,
                                                 c->n_count.as<int>(), c->t_off.as<int>(),
                                                 nullptr, c->t_cur.as<int4>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
-  int nfs_total = 0, nfp_total = 0;
-  size_t fs_cap = 0, fp_cap = 0;
-  DBuf fs_buf, fp_buf;
-  while (nt > 0) {
-    SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (3 * (size_t)(nt + 1) + 1)));
-    SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (3 * (size_t)(nt + 1) + 1)));
+  SPH_CUDA(cudaMemcpyAsync(ntp, c->t_off.as<int>() + ntop, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  SPH_CUDA(cudaMemsetAsync(fin_len, 0, 2 * sizeof(int), s));
+  for (int g = 0; g < ngen; ++g) {
+    const int cap = 14 * (c->gen_start[g + 1] - c->gen_start[g]);
+    if (cap <= 0) continue;
     int* nch = c->t_cnt.as<int>();
-    int* nfs = nch + (nt + 1);
-    int* nfp = nfs + (nt + 1);
+    int* nfs = nch + (cap + 1);
+    int* nfp = nfs + (cap + 1);
     int* och = c->t_off.as<int>();
-    int* ofs = och + (nt + 1);
-    int* ofp = ofs + (nt + 1);
-    // the three counts side by side (zero gaps) take one scan: the self and
-    // pair offsets then carry the totals before them
-    SPH_CUDA(cudaMemsetAsync(nch, 0, sizeof(int) * 3 * (size_t)(nt + 1), s));
-    { k_refine<<<div_up(nt, TPB), TPB, 0, s>>>(
-        nt, c->t_cur.as<int4>(), c->n_child0.as<int>(), c->n_count.as<int>(),
+    int* ofs = och + (cap + 1);
+    int* ofp = ofs + (cap + 1);
+    SPH_CUDA(cudaMemsetAsync(nch, 0, sizeof(int) * 3 * (size_t)(cap + 1), s));
+    { k_refine<<<div_up(cap, TPB), TPB, 0, s>>>(
+        ntp, cap, c->t_cur.as<int4>(), c->n_child0.as<int>(), c->n_count.as<int>(),
         c->n_hbuild.as<float>(), c->n_ijk.as<int4>(), c->n_box.as<int>(), c->d_box_L.as<double>(),
-        nch, nfs, nfp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr); note_launch(); }
+        nch, nfs, nfp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr); note_launch(); }
     SPH_CUDA(cudaGetLastError());
-    SPH_TRY(scan_exclusive_i32(nch, och, 3 * (nt + 1), och + 3 * (nt + 1), c->scan_tmp, s));
-    int cum[3];
-    SPH_CUDA(cudaMemcpyAsync(&cum[0], och + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaMemcpyAsync(&cum[1], ofs + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaMemcpyAsync(&cum[2], ofp + nt, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(cudaStreamSynchronize(s));
-    const int tot[3] = {cum[0], cum[1] - cum[0], cum[2] - cum[1]};
-    SPH_TRY(dbuf_ensure(c->t_next, sizeof(int4) * (size_t)(tot[0] + 1)));
-    if ((size_t)(nfs_total + tot[1]) > fs_cap) {
-      fs_cap = (size_t)(nfs_total + tot[1]) * 2 + 1024;
-      SPH_TRY(grow_copy(fs_buf, sizeof(int) * nfs_total, sizeof(int) * fs_cap, s));
-    }
-    if ((size_t)(nfp_total + tot[2]) > fp_cap) {
-      fp_cap = (size_t)(nfp_total + tot[2]) * 2 + 1024;
-      SPH_TRY(grow_copy(fp_buf, sizeof(int4) * nfp_total, sizeof(int4) * fp_cap, s));
-    }
-    { k_refine<<<div_up(nt, TPB), TPB, 0, s>>>(
-        nt, c->t_cur.as<int4>(), c->n_child0.as<int>(), c->n_count.as<int>(),
+    SPH_TRY(scan_exclusive_i32(nch, och, 3 * (cap + 1), och + 3 * (cap + 1), c->scan_tmp, s));
+    { k_refine<<<div_up(cap, TPB), TPB, 0, s>>>(
+        ntp, cap, c->t_cur.as<int4>(), c->n_child0.as<int>(), c->n_count.as<int>(),
         c->n_hbuild.as<float>(), c->n_ijk.as<int4>(), c->n_box.as<int>(), c->d_box_L.as<double>(),
-        nullptr, nullptr, nullptr, och, ofs, ofp, c->t_next.as<int4>(), fs_buf.as<int>(),
-        fp_buf.as<int4>(), nfs_total - cum[0], nfp_total - cum[1], c->n_flags.as<int>()); note_launch(); }
+        nullptr, nullptr, nullptr, och, ofs, ofp, c->t_next.as<int4>(), c->t_final_self.as<int>(),
+        c->t_final_pair.as<int4>(), fin_len, c->n_flags.as<int>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
-    nfs_total += tot[1];
-    nfp_total += tot[2];
+    { k_refine_advance<<<1, 1, 0, s>>>(cap, och, ofs, ofp, ntp, fin_len); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
     std::swap(c->t_cur, c->t_next);
-    nt = tot[0];
   }
-  dbuf_free(c->t_final_self);
-  dbuf_free(c->t_final_pair);
-  c->t_final_self = fs_buf;
-  c->t_final_pair = fp_buf;
-  c->nself = nfs_total;
-  c->npair = nfp_total;
+  int fl[3] = {0, 0, 0};
+  SPH_CUDA(cudaMemcpyAsync(fl, ntp, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
+  if (fl[0] != 0) return SPH_ERR_INVALID_ARG;  // tasks left below the deepest generation
+  c->nself = fl[1];
+  c->npair = fl[2];
   // cell limits
   SPH_TRY(dbuf_ensure(c->n_hlim, sizeof(float) * ncell));
   for (size_t g = 0; g + 1 < c->gen_start.size(); ++g) {

@@ -117,6 +117,7 @@ struct sph_ctx {
   DBuf t_final_pair;         // int4 {ci, cj, packed offset/periodic, 0}
   DBuf t_final_self;         // int
   DBuf t_cnt, t_cnt2, t_off, t_off2;
+  DBuf task_ctl;             // int: tasks of the current generation, final self and pair counts
 
   // blocks
   int nblock = 0, nleaf = 0;
