@@ -420,7 +420,7 @@ void sph_destroy(sph_ctx* c) {
                  &c->prof_units, &c->solve_ctl, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
                  &c->tmp_b, &c->tmp_c, &c->p_et, &c->nleaf_dev, &c->n_listed, &c->n_ex, &c->n_lo,
                  &c->n_hi, &c->b_lo, &c->b_hi, &c->fl_list, &c->fl_cnt, &c->fl_flag, &c->fl_blk,
-                 &c->fl_over, &c->task_ctl};
+                 &c->fl_over, &c->task_ctl, &c->tree_ctl};
   for (DBuf* b : all) dbuf_free(*b);
   for (auto& e : c->ev_pending) {
     cudaEventDestroy(e.a);
@@ -428,6 +428,7 @@ void sph_destroy(sph_ctx* c) {
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   graph_release(c);
+  if (c->tree_host) cudaFreeHost(c->tree_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }

@@ -37,6 +37,7 @@ __device__ __forceinline__ int box_of_node(const int* top_base, int nbox, int id
 }
 
 __device__ __forceinline__ double wrap_pos(double x, double L) {
+  if (x >= 0.0 && x < L) return x;  // inside the box already (no FP64 division)
   double w = x - L * floor(x / L);
   if (w >= L) w -= L;
   if (w < 0) w = 0;
@@ -123,12 +124,19 @@ __global__ void k_init_top(int ntop, const int* top_base, const int* box_t, int 
 
 // structural fields of the 8 children of each split node; their particle
 // ranges are filled by k_pcur_update from the Morton-key boundaries
-__global__ void k_make_children(int g0, int g1, int next, const int* split, const int* soff,
-                                NodeArrays na) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int node = g0 + i;
-  if (node >= g1 || !split[i]) return;
-  int c0 = next + 8 * soff[i];
+// children of the splitting nodes of the generation, placed after it in
+// split order; ctl[2] is set (and nothing created) when they would not fit
+__global__ void k_make_children(int* ctl, int ngmax, int cap, const int* split, const int* soff,
+                                NodeArrays na, int* acc_h, int* acc_s, int* cend) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g0 = ctl[0], g1 = ctl[1];
+  if ((long long)g1 + 8ll * soff[ngmax] > (long long)cap) {
+    if (i == 0) ctl[2] = 1;
+    return;
+  }
+  const int node = g0 + i;
+  if (i >= ngmax || node >= g1 || !split[i]) return;
+  int c0 = g1 + 8 * soff[i];
   na.child0[node] = c0;
   int4 p = na.ijk[node];
   int b = na.box[node];
@@ -143,6 +151,9 @@ __global__ void k_make_children(int g0, int g1, int next, const int* split, cons
     na.top[id] = na.top[node];
     na.box[id] = b;
     na.ijk[id] = make_int4(cx, cy, cz, lvl);
+    acc_h[id] = 0;
+    acc_s[id] = 0;
+    cend[id] = 0;
   }
 }
 
@@ -196,20 +207,18 @@ __global__ void k_h_estimate_flat(long long n, const unsigned long long* keys, i
   const double L = Ls[b];
   const int shl = 3 * (K - Ll);
   const long long cl = first_gt(keys, s + 1, n, key >> shl, shl) - first_ge(keys, 0, s, key >> shl, shl);
-  const double el = L / (double)(1ll << Ll);
-  double dens;
+  // number densities count / edge^3 with edge = L 2^-level (FP32 suffices
+  // for an estimate)
+  const float iv = 1.0f / (float)(L * L * L);
+  float dens = (float)cl * ldexpf(iv, 3 * Ll);
   if (Ll > t0) {
     const int Lp = Ll - 1, shp = 3 * (K - Lp);
     const long long cp = first_gt(keys, s + 1, n, key >> shp, shp) - first_ge(keys, 0, s, key >> shp, shp);
-    const double ep = L / (double)(1ll << Lp);
-    dens = (double)cp / (ep * ep * ep);
-    if (mode == 1 && cl >= 8) dens = fmin(dens, (double)cl / (el * el * el));
-  } else {
-    dens = (double)cl / (el * el * el);
+    const float dp = (float)cp * ldexpf(iv, 3 * Lp);
+    dens = (mode == 1 && cl >= 8) ? fminf(dp, dens) : dp;
   }
-  double h = (double)factor * cbrt(3.0 * (double)n_ngb / (4.0 * M_PI * dens));
-  h = fmin(h, 0.24 * L);
-  hout[s] = (float)h;
+  const float h = factor * cbrtf((float)(3.0 * (double)n_ngb / (4.0 * M_PI)) / dens);
+  hout[s] = fminf(h, (float)(0.24 * L));
 }
 
 __global__ void k_scale(long long n, float* v, float f) {
@@ -226,7 +235,7 @@ __global__ void k_relpos(long long n, const unsigned long long* keys, const doub
   int t = box_t[b];
   unsigned long long tm = (key >> (3 * (K - t))) & ((1ull << (3 * t)) - 1);
   int ix = compact3(tm >> 2), iy = compact3(tm >> 1), iz = compact3(tm);
-  double e = Ls[b] / (double)(1 << t);
+  double e = ldexp(Ls[b], -t);
   float4 v;
   v.x = (float)(xs[3 * s + 0] - ix * e);
   v.y = (float)(xs[3 * s + 1] - iy * e);
@@ -275,7 +284,7 @@ __global__ void k_top_tasks(int ntop, const int* top_base, const int* box_t, int
 __device__ __forceinline__ bool pair_splits(int a, int b, const int* child0, const float* hb,
                                             const int4* ijk, const int* box, const double* Ls) {
   if (child0[a] < 0 || child0[b] < 0) return false;
-  double e = Ls[box[a]] / (double)(1ll << ijk[a].w);
+  double e = ldexp(Ls[box[a]], -ijk[a].w);
   float half = (float)(0.5 * e);
   return hb[a] <= half && hb[b] <= half;
 }
@@ -373,10 +382,10 @@ __global__ void k_hlim(int g0, int g1, const int* parent, const int* psplit, con
   int p = parent[node];
   double L = Ls[box[node]];
   if (p < 0) {
-    hlim[node] = (float)(L / (double)(1ll << ijk[node].w));
+    hlim[node] = (float)(ldexp(L, -ijk[node].w));
   } else {
     float v = hlim[p];
-    if (psplit[p]) v = fminf(v, (float)(0.5 * L / (double)(1ll << ijk[p].w)));
+    if (psplit[p]) v = fminf(v, (float)(0.5 * ldexp(L, -ijk[p].w)));
     hlim[node] = v;
   }
 }
@@ -732,7 +741,7 @@ __global__ void k_block_dts(int nblock, const int* b_leaf, const int* b_count, c
                   parent, ncount, nblk, blk0, b_count, dt_cj, dt_code, dt_shift, c, wb);
   int bx = box[leaf];
   double L = Ls[bx];
-  double et = L / (double)(1 << box_t[bx]);
+  double et = ldexp(L, -box_t[bx]);
   int4 ta = ijk[ntop[leaf]];
   for (int a = leaf; a >= 0; a = parent[a]) {
     for (int k = 0; k < deg[a]; ++k) {
@@ -787,38 +796,36 @@ __global__ void k_stats_flat(long long n, const int* pcur, const float* hs, cons
   int hb = 0, small = 0;
   if (node >= 0 && use_h) {
     float hv = hs[s];
-    double e = Ls[box[node]] / (double)(1ll << ijk[node].w);
+    double e = ldexp(Ls[box[node]], -ijk[node].w);
     hb = __float_as_int(hv);
     small = hv < (float)(0.5 * e) ? 1 : 0;
   }
   unsigned peers = __match_any_sync(0xffffffffu, node);
   int leader = __ffs(peers) - 1;
-  // reduce within the peer group
-  int mh = hb, ms = small;
-  unsigned rest = peers;
-  int sum = 0, mx = 0;
-  while (rest) {
-    int l = __ffs(rest) - 1;
-    rest &= rest - 1;
-    int a = __shfl_sync(peers, mh, l);
-    int b = __shfl_sync(peers, ms, l);
-    mx = max(mx, a);
-    sum += b;
-  }
+  // reduce within the peer group (h bits of positive floats order as ints)
+  const int mx = __reduce_max_sync(peers, hb);
+  const int sum = __reduce_add_sync(peers, small);
   if (lane == leader && node >= 0) {
     if (use_h) atomicMax(&acc_hmax[node], mx);
     atomicAdd(&acc_small[node], sum);
   }
 }
 
-__global__ void k_split_decide(int g0, int g1, int split_count, float split_frac, int K,
+// generation bounds live on the device: ctl[0] = first node of the
+// generation, ctl[1] = one past its last node
+__global__ void k_split_decide(const int* ctl, int ngmax, int split_count, float split_frac, int K,
                                const int* count, const int4* ijk, const int* acc_hmax,
                                const int* acc_small, float* hbuild, int* split) {
-  int node = g0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= g1) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ngmax) return;
+  const int node = ctl[0] + i;
+  if (node >= ctl[1]) {
+    split[i] = 0;
+    return;
+  }
   int c = count[node];
   hbuild[node] = __int_as_float(acc_hmax[node]);
-  split[node - g0] =
+  split[i] =
       (c > split_count) && ((float)acc_small[node] > split_frac * (float)c) && (ijk[node].w < K);
 }
 
@@ -848,11 +855,34 @@ __global__ void k_pcur_update(long long n, int* pcur, const unsigned long long* 
   if (s == e - 1 || (int)((keys[s + 1] >> sh) & 7ull) != k) cend[child] = (int)(s + 1);
 }
 
-__global__ void k_child_counts(int c0, int c1, const int* cend, int* first, int* count) {
-  int id = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= c1) return;
+__global__ void k_child_counts(const int* ctl, int ngmax, const int* soff, const int* cend,
+                               int* first, int* count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ctl[2] || i >= 8 * soff[ngmax]) return;
+  const int id = ctl[1] + i;
   int e = cend[id];
   count[id] = e > 0 ? e - first[id] : 0;
+}
+
+// next generation: ctl[3] is the last generation holding nodes, ctl[4 + g]
+// is where generation g starts (ctl[5 + ctl[3]] where the tree ends)
+__global__ void k_tree_advance(int* ctl, int ngmax, const int* soff) {
+  if (ctl[2]) return;
+  const int nsplit = soff[ngmax];
+  if (nsplit == 0) return;
+  ctl[0] = ctl[1];
+  ctl[1] += 8 * nsplit;
+  ctl[3] += 1;
+  ctl[5 + ctl[3]] = ctl[1];
+}
+
+__global__ void k_tree_init(int* ctl, int ntop) {
+  ctl[0] = 0;     // generation 0: the top cells
+  ctl[1] = ntop;
+  ctl[2] = 0;     // overflow
+  ctl[3] = 0;     // last generation holding nodes
+  ctl[4] = 0;     // generation starts
+  ctl[5] = ntop;
 }
 
 __global__ void k_box_hmax(long long n, const long long* off, int nbox, const float* h, int* out) {
@@ -861,13 +891,7 @@ __global__ void k_box_hmax(long long n, const long long* off, int nbox, const fl
   int b = s < n ? box_of(off, nbox, s) : -1;
   int v = s < n ? __float_as_int(h[s]) : 0;
   unsigned peers = __match_any_sync(0xffffffffu, b);
-  unsigned rest = peers;
-  int mx = 0;
-  while (rest) {
-    int l = __ffs(rest) - 1;
-    rest &= rest - 1;
-    mx = max(mx, __shfl_sync(peers, v, l));
-  }
+  const int mx = __reduce_max_sync(peers, v);
   if (lane == __ffs(peers) - 1 && b >= 0) atomicMax(&out[b], mx);
 }
 
@@ -1162,76 +1186,104 @@ static int build_tree(sph_ctx* c, cudaStream_t s) {
                            cudaMemcpyHostToDevice, s));
   SPH_CUDA(cudaMemcpyAsync(c->d_box_t.p, c->box_t.data(), sizeof(int) * c->nbox,
                            cudaMemcpyHostToDevice, s));
-  NodeBufs nbufs{c};
-  size_t cap0 = (size_t)c->ntop + 8 * ((size_t)n / 64 + 16);
-  SPH_TRY(nbufs.grow(0, cap0, s));
-  NodeArrays na = nbufs.arrays();
-  { k_init_top<<<div_up(c->ntop, TPB), TPB, 0, s>>>(c->ntop, c->d_top_base.as<int>(),
-                                                  c->d_box_t.as<int>(), c->nbox,
-                                                  c->keys.as<unsigned long long>(), n, K, na); note_launch(); }
-  SPH_CUDA(cudaGetLastError());
-  c->gen_start.assign(1, 0);
-  c->gen_start.push_back(c->ntop);
-  int g0 = 0, g1 = c->ntop;
-  int maxd = 0;
-  for (int b = 0; b < c->nbox; ++b) maxd = std::max(maxd, c->box_t[b]);
+  // Node capacity: the nodes of one generation are disjoint and a node splits
+  // only above split_count particles, so a generation has at most
+  // max(ntop, 8 (n / (split_count + 1) + 1)) nodes; the total is kept from
+  // build to build and doubled (with the tree rebuilt) if it runs out.
+  // Generation bounds, counts and the overflow flag live on the device, so
+  // the generations are enqueued without host round trips; the host stops
+  // enqueueing once a finished generation reports that nothing split.
+  const int ngmax = std::max(c->ntop, 8 * (n / (c->prm.split_count + 1) + 1));
+  int mint = 64, maxt = 0;
+  for (int b = 0; b < c->nbox; ++b) {
+    mint = std::min(mint, c->box_t[b]);
+    maxt = std::max(maxt, c->box_t[b]);
+  }
+  const int maxgen = K - mint + 1;
+  if (c->node_cap < (size_t)c->ntop + (size_t)ngmax)
+    c->node_cap = (size_t)c->ntop + 4 * (size_t)ngmax;
   SPH_TRY(dbuf_ensure(c->pnode, sizeof(int) * (size_t)n));
   SPH_TRY(dbuf_ensure(c->tmp_c, sizeof(int) * (size_t)n));  // pcur
+  SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * ((size_t)ngmax + 1)));
+  SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * ((size_t)ngmax + 1)));
+  SPH_TRY(dbuf_ensure(c->tree_ctl, sizeof(int) * (size_t)(8 + maxgen + 2)));
+  if (!c->tree_host) SPH_CUDA(cudaHostAlloc(&c->tree_host, 4096, cudaHostAllocDefault));
   int* pcur = c->tmp_c.as<int>();
-  { k_pcur_init<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), c->d_box_t.as<int>(),
-                                              c->d_top_base.as<int>(), K, pcur); note_launch(); }
-  SPH_CUDA(cudaGetLastError());
+  int* ctl = c->tree_ctl.as<int>();
   for (;;) {
-    int ng = g1 - g0;
-    SPH_TRY(dbuf_ensure(c->t_cnt, sizeof(int) * (ng + 1)));
-    SPH_TRY(dbuf_ensure(c->t_off, sizeof(int) * (ng + 1)));
-    SPH_TRY(grow_copy(c->n_flags, sizeof(int) * (size_t)g0, sizeof(int) * (size_t)g1 + 64, s));
-    SPH_TRY(grow_copy(c->n_need, sizeof(int) * (size_t)g0, sizeof(int) * (size_t)g1 + 64, s));
-    int* acc_h = c->n_flags.as<int>();   // scratch during the build: max h bits
-    int* acc_s = c->n_need.as<int>();    // scratch during the build: small-h counts
-    SPH_CUDA(cudaMemsetAsync(acc_h + g0, 0, sizeof(int) * ng, s));
-    SPH_CUDA(cudaMemsetAsync(acc_s + g0, 0, sizeof(int) * ng, s));
-    na = nbufs.arrays();
-    { k_stats_flat<<<div_up(n, TPB), TPB, 0, s>>>(n, pcur, c->hguess.as<float>(), na.ijk, na.box,
-                                                 c->d_box_L.as<double>(), 1, acc_h, acc_s); note_launch(); }
+    const size_t cap = c->node_cap;
+    NodeBufs nbufs{c};
+    SPH_TRY(nbufs.grow(0, cap, s));
+    SPH_TRY(dbuf_ensure(c->n_flags, sizeof(int) * cap));
+    SPH_TRY(dbuf_ensure(c->n_need, sizeof(int) * cap));
+    SPH_TRY(dbuf_ensure(c->t_cnt2, sizeof(int) * cap));
+    int* acc_h = c->n_flags.as<int>();  // scratch during the build: max h bits
+    int* acc_s = c->n_need.as<int>();   // scratch during the build: small-h counts
+    int* cend = c->t_cnt2.as<int>();
+    NodeArrays na = nbufs.arrays();
+    { k_init_top<<<div_up(c->ntop, TPB), TPB, 0, s>>>(c->ntop, c->d_top_base.as<int>(),
+                                                    c->d_box_t.as<int>(), c->nbox,
+                                                    c->keys.as<unsigned long long>(), n, K, na); note_launch(); }
     SPH_CUDA(cudaGetLastError());
-    { k_split_decide<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, c->prm.split_count,
-                                                    c->prm.split_frac, K, na.count, na.ijk, acc_h,
-                                                    acc_s, na.hbuild, c->t_cnt.as<int>()); note_launch(); }
+    SPH_CUDA(cudaMemsetAsync(acc_h, 0, sizeof(int) * (size_t)c->ntop, s));
+    SPH_CUDA(cudaMemsetAsync(acc_s, 0, sizeof(int) * (size_t)c->ntop, s));
+    { k_tree_init<<<1, 1, 0, s>>>(ctl, c->ntop); note_launch(); }
     SPH_CUDA(cudaGetLastError());
-    SPH_TRY(scan_exclusive_i32(c->t_cnt.as<int>(), c->t_off.as<int>(), ng,
-                               c->t_off.as<int>() + ng, c->scan_tmp, s));
-    int nsplit = 0;
-    SPH_TRY(d2h(&nsplit, c->t_off.as<int>() + ng, s));
-    int* cend = nullptr;
-    if (nsplit > 0) {
-      SPH_TRY(nbufs.grow((size_t)g1, (size_t)g1 + 8 * (size_t)nsplit, s));
-      na = nbufs.arrays();
-      { k_make_children<<<div_up(ng, TPB), TPB, 0, s>>>(g0, g1, g1, c->t_cnt.as<int>(),
-                                                       c->t_off.as<int>(), na); note_launch(); }
+    { k_pcur_init<<<div_up(n, TPB), TPB, 0, s>>>(n, c->keys.as<unsigned long long>(), c->d_box_t.as<int>(),
+                                                c->d_top_base.as<int>(), K, pcur); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+    int* hdone = reinterpret_cast<int*>(c->tree_host);
+    std::vector<cudaEvent_t> evs;
+    for (int g = 0; g < maxgen; ++g) {
+      // stop once an earlier, finished generation reported no split
+      bool done = false;
+      for (int k = 0; k < (int)evs.size(); ++k)
+        if (cudaEventQuery(evs[k]) == cudaSuccess && hdone[k] == 0) done = true;
+      if (done) break;
+      { k_stats_flat<<<div_up(n, TPB), TPB, 0, s>>>(n, pcur, c->hguess.as<float>(), na.ijk, na.box,
+                                                   c->d_box_L.as<double>(), 1, acc_h, acc_s); note_launch(); }
       SPH_CUDA(cudaGetLastError());
-      SPH_TRY(grow_copy(c->t_cnt2, 0, sizeof(int) * ((size_t)g1 + 8 * (size_t)nsplit), s));
-      cend = c->t_cnt2.as<int>();
-      SPH_CUDA(cudaMemsetAsync(cend + g1, 0, sizeof(int) * 8 * (size_t)nsplit, s));
-    }
-    { k_pcur_update<<<div_up(n, TPB), TPB, 0, s>>>(n, pcur, c->keys.as<unsigned long long>(),
-                                                  na.child0, na.first, na.count, na.ijk, K,
-                                                  c->pnode.as<int>(), na.first, cend); note_launch(); }
-    SPH_CUDA(cudaGetLastError());
-    if (nsplit > 0) {
-      { k_child_counts<<<div_up(8 * nsplit, TPB), TPB, 0, s>>>(g1, g1 + 8 * nsplit, cend, na.first,
-                                                              na.count); note_launch(); }
+      { k_split_decide<<<div_up(ngmax, TPB), TPB, 0, s>>>(ctl, ngmax, c->prm.split_count,
+                                                         c->prm.split_frac, K, na.count, na.ijk,
+                                                         acc_h, acc_s, na.hbuild, c->t_cnt.as<int>()); note_launch(); }
       SPH_CUDA(cudaGetLastError());
+      SPH_TRY(scan_exclusive_i32(c->t_cnt.as<int>(), c->t_off.as<int>(), ngmax,
+                                 c->t_off.as<int>() + ngmax, c->scan_tmp, s));
+      { k_make_children<<<div_up(ngmax, TPB), TPB, 0, s>>>(ctl, ngmax, (int)cap, c->t_cnt.as<int>(),
+                                                          c->t_off.as<int>(), na, acc_h, acc_s, cend); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+      { k_pcur_update<<<div_up(n, TPB), TPB, 0, s>>>(n, pcur, c->keys.as<unsigned long long>(),
+                                                    na.child0, na.first, na.count, na.ijk, K,
+                                                    c->pnode.as<int>(), na.first, cend); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+      { k_child_counts<<<div_up(ngmax, TPB), TPB, 0, s>>>(ctl, ngmax, c->t_off.as<int>(), cend,
+                                                         na.first, na.count); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+      { k_tree_advance<<<1, 1, 0, s>>>(ctl, ngmax, c->t_off.as<int>()); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+      {
+        cudaEvent_t e = ev_get(c);
+        if (!e) return SPH_ERR_CUDA;
+        SPH_CUDA(cudaMemcpyAsync(hdone + evs.size(), c->t_off.as<int>() + ngmax, sizeof(int),
+                                 cudaMemcpyDeviceToHost, s));
+        SPH_CUDA(cudaEventRecord(e, s));
+        evs.push_back(e);
+      }
     }
-    if (nsplit == 0) break;
-    g0 = g1;
-    g1 += 8 * nsplit;
-    c->gen_start.push_back(g1);
-    ++maxd;
+    int hc[8 + 64];
+    SPH_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(int) * (size_t)(4 + maxgen + 2), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+    for (cudaEvent_t e : evs) c->ev_pool.push_back(e);
+    if (hc[2]) {  // out of node capacity: double it and build again
+      c->node_cap *= 2;
+      continue;
+    }
+    const int ngen = hc[3] + 1;  // generations holding nodes
+    c->gen_start.assign(hc + 4, hc + 4 + ngen + 1);
+    c->ncell = hc[1];
+    c->max_depth = maxt + ngen - 1;
+    return SPH_OK;
   }
-  c->ncell = g1;
-  c->max_depth = maxd;
-  return SPH_OK;
 }
 
 static int choose_top_levels(sph_ctx* c, cudaStream_t s) {

@@ -118,6 +118,9 @@ struct sph_ctx {
   DBuf t_final_self;         // int
   DBuf t_cnt, t_cnt2, t_off, t_off2;
   DBuf task_ctl;             // int: tasks of the current generation, final self and pair counts
+  DBuf tree_ctl;             // int: generation bounds, overflow flag, generation starts
+  size_t node_cap = 0;       // octree node capacity (kept from build to build)
+  void* tree_host = nullptr; // pinned: per-generation split counts read back while enqueueing
 
   // blocks
   int nblock = 0, nleaf = 0;
