@@ -793,6 +793,7 @@ __global__ void k_stats_flat(long long n, const int* pcur, const float* hs, cons
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int node = s < n ? pcur[s] : -1;
+  if (__all_sync(0xffffffffu, node < 0)) return;  // every particle here sits in a leaf
   int hb = 0, small = 0;
   if (node >= 0 && use_h) {
     float hv = hs[s];
