@@ -175,6 +175,24 @@ def oracle_sample_rate(d, seconds_target=15.0, seed=0, sample=None):
     return dict(value=units / dt, seconds=dt, sample=int(S), units=units)
 
 
+def max_over_ranks(x, device=None):
+    """The largest of every rank's x (all ranks get it); x itself on one rank.
+    The timed region of a step ends when the slowest replica ends."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_per_step):
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank per step, the step lasting ms_per_step (max over ranks)."""
+    return units_per_rank * world / (ms_per_step / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -337,10 +355,7 @@ def main():
         adj = float(np.mean([a.elapsed_time(b) for a, b in zip(ev["f1"], ev["a1"])]))
         stats = sph.stats()
         sph.profile(False)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         return dict(ms=ms, fwd=fwd, adj=adj, launches=launches, stats=stats, clocks=clocks)
 
     # production pass: device-side graphs for the h iteration, no profiling
@@ -350,7 +365,7 @@ def main():
     ms, fwd_ms, adj_ms, launches, clocks = (prod["ms"], prod["fwd"], prod["adj"], prod["launches"],
                                             prod["clocks"])
     st = prof["stats"]
-    value = units * world / (ms / 1e3)
+    value = job_rate(units, world, ms)
 
     # ---- end to end through the public API: pinned host inputs, host outputs
     hpos = torch.tensor(d["x"], dtype=torch.float64).pin_memory()
@@ -358,6 +373,8 @@ def main():
     hu = torch.tensor(d["u"]).pin_memory()
     hv = torch.tensor(d["v"]).pin_memory()
     outs_host = None
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -371,7 +388,9 @@ def main():
         outs_host = [t.to("cpu", non_blocking=True) for t in (den["rho"], den["h"], acc, dudt, g_pos, g_m, g_u)]
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        torch.distributed.barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     h2d = sum(t.numel() * t.element_size() for t in (hpos, hm, hu, hv))
     d2h = sum(t.numel() * t.element_size() for t in outs_host)
 
@@ -461,7 +480,7 @@ def main():
             "fwd_ms": fwd_ms, "adj_ms": adj_ms, "fwd_adj_over_fwd": (fwd_ms + adj_ms) / fwd_ms,
             "fwd_value": units / (fwd_ms / 1e3),
             "clocks": clocks,
-            "e2e": {"value": units * world / (e2e_ms / 1e3), "unit": UNIT,
+            "e2e": {"value": job_rate(units, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "profiled_pass": {"ms_per_step": prof["ms"], "gpu_launches": int(prof["launches"]),
