@@ -21,6 +21,9 @@ Section 2.1):
   (text after Eq. (dudt)), gamma = 5/3;
 * dv_i/dt, Eq. (dvdt), over r_ij < max(h_i, h_j), and du_i/dt, Eq. (dudt),
   over r_ij < h_i, with grad W(r, h) = dW/dr (x_i - x_j)/r (zero at r = 0);
+* the Monaghan-Balsara artificial viscosity added to Eq. (dvdt) and
+  Eq. (dudt), the velocity divergence and curl it needs, and the time-step
+  criterion Eq. (dt) (Section 4.1; readings beside the code);
 * the reverse-mode gradient of any linear functional of (rho, dv/dt, du/dt)
   with respect to positions, masses and internal energies, with h
   differentiated implicitly through N_i(h_i, x) = N_ngb.  The paper has no
@@ -557,3 +560,105 @@ def pairs_fp32(x, h32, phase="density", box=1.0):
     else:
         keep = (I != j) & ((r2 < h2[I]) | (r2 < h2[j]))
     return np.unique(I[keep] * n + j[keep])
+
+
+# --------------------------------------------------------------------------
+# Artificial viscosity and the time-step criterion (Section 4.1: the
+# Monaghan-Balsara terms added to Eq. (dvdt) and Eq. (dudt), and Eq. (dt)).
+# Readings where the printed formulas are garbled or silent:
+#   * the switch is Balsara's, f_i = |div v_i| / (|div v_i| + |curl v_i|
+#     + 1e-4 c_i/h_i): the printed numerator |curl v_i| would switch the
+#     viscosity on in pure shear and off in pure compression, the opposite
+#     of its stated purpose, and the printed c_j/h_j has no j in scope;
+#   * c_i = sqrt(gamma (gamma - 1) u_i), the ideal-gas sound speed;
+#   * the viscous sums run over the pressure force's pair set,
+#     r_ij < max(h_i, h_j) (the printed h-hat_ij);
+#   * div v_i and curl v_i sum over the density loop's set r_ij < h_i (the
+#     self term contributes nothing: v_i - v_i = 0);
+#   * the maximum in Eq. (dt) runs over the same force pairs; a particle
+#     with none takes c_i + c_i.
+# --------------------------------------------------------------------------
+def sound_speed(u, gamma=GAMMA):
+    """c_i = sqrt(gamma (gamma - 1) u_i)."""
+    return np.sqrt(gamma * (gamma - 1.0) * np.asarray(u, dtype=np.float64))
+
+
+def velocity_derivatives(nb: Neighbours, m, v, h, rho):
+    """div v_i = (1/rho_i) sum_j m_j (v_j - v_i) . grad W(r_ij, h_i) and
+    curl v_i = -(1/rho_i) sum_j m_j (v_j - v_i) x grad W(r_ij, h_i) over
+    r_ij < h_i, with grad W = G(r, h) (x_i - x_j)/r (Section 4.1)."""
+    n = nb.x.shape[0]
+    m = np.asarray(m, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    i, j, d, r = directed_pairs(nb, h)
+    pos = r > 0
+    i, j, d, r = i[pos], j[pos], d[pos], r[pos]
+    gw = (G(r, h[i]) / r)[:, None] * d                   # grad_i W(r_ij, h_i)
+    dv = v[j] - v[i]
+    div = np.bincount(i, weights=m[j] * np.einsum("ij,ij->i", dv, gw), minlength=n) / rho
+    cr = np.cross(dv, gw) * m[j][:, None]
+    curl = -np.stack([np.bincount(i, weights=cr[:, k], minlength=n) for k in range(3)],
+                     axis=1) / rho[:, None]
+    return div, curl
+
+
+def balsara(div, curl, c, h):
+    """f_i = |div v_i| / (|div v_i| + |curl v_i| + 1e-4 c_i/h_i)."""
+    ad = np.abs(div)
+    ac = np.linalg.norm(curl, axis=1)
+    return ad / (ad + ac + 1e-4 * c / h)
+
+
+def viscosity_from_pairs(I, J, d, r, n, m, v, h, rho, c, f, alpha):
+    """The viscous terms over the ordered force pairs (I, J), rows I:
+    dv_i/dt += -(1/4) sum_j m_j Pi_ij (grad W(r,h_i) + grad W(r,h_j)) (f_i + f_j),
+    du_i/dt += (1/8) sum_j m_j Pi_ij v_ij . (grad W(r,h_i) + grad W(r,h_j)) (f_i + f_j),
+    Pi_ij = -alpha (c_i + c_j - 3 w_ij) w_ij / (rho_i + rho_j),
+    w_ij = min(0, v_ij . r_ij / r_ij), v_ij = v_i - v_j (Section 4.1)."""
+    m = np.asarray(m, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    pos = r > 0
+    I, J, d, r = I[pos], J[pos], d[pos], r[pos]
+    xhat = d / r[:, None]
+    vij = v[I] - v[J]
+    wij = np.minimum(0.0, np.einsum("ij,ij->i", vij, xhat))
+    Pi = -alpha * (c[I] + c[J] - 3.0 * wij) * wij / (rho[I] + rho[J])
+    gsum = (G(r, h[I]) + G(r, h[J]))[:, None] * xhat     # grad W_i + grad W_j
+    fs = f[I] + f[J]
+    ca = -0.25 * (m[J] * Pi * fs)[:, None] * gsum
+    a = np.stack([np.bincount(I, weights=ca[:, k], minlength=n) for k in range(3)], axis=1)
+    e = 0.125 * m[J] * Pi * fs * np.einsum("ij,ij->i", vij, gsum)
+    du = np.bincount(I, weights=e, minlength=n)
+    return a, du
+
+
+def cfl_dt(I, J, d, r, n, v, h, c, c_cfl):
+    """Eq. (dt): dt_i = C_CFL 2 h_i / max_j (c_i + c_j + max(0, -3 r_ij . v_ij / r_ij))
+    over the force pairs (I, J); c_i + c_i for a particle without any."""
+    v = np.asarray(v, dtype=np.float64)
+    sig = 2.0 * c.copy()
+    pos = r > 0
+    I, J, d, r = I[pos], J[pos], d[pos], r[pos]
+    rv = np.einsum("ij,ij->i", d, v[I] - v[J]) / r
+    s = c[I] + c[J] + np.maximum(0.0, -3.0 * rv)
+    vmax = np.full(n, -np.inf)
+    np.maximum.at(vmax, I, s)
+    has = np.isfinite(vmax)
+    sig[has] = vmax[has]
+    return c_cfl * 2.0 * h / sig
+
+
+def evaluate_viscosity(fwd, x, m, u, v, alpha=0.8, c_cfl=0.25, gamma=GAMMA):
+    """Viscous accelerations and heating, the Balsara switch, div/curl v and
+    the time steps at the solved h of ``fwd`` (an ``evaluate`` result).
+    alpha = 0.8 and C_CFL = 1/4 are the values of the paper's runs."""
+    nb = fwd["nb"]
+    n = nb.x.shape[0]
+    h, rho = fwd["h"], fwd["rho"]
+    c = sound_speed(u, gamma)
+    div, curl = velocity_derivatives(nb, m, v, h, rho)
+    f = balsara(div, curl, c, h)
+    I, J, d, r = force_pairs_all(nb, h)
+    a, du = viscosity_from_pairs(I, J, d, r, n, m, v, h, rho, c, f, alpha)
+    dt = cfl_dt(I, J, d, r, n, v, h, c, c_cfl)
+    return dict(a_visc=a, dudt_visc=du, div=div, curl=curl, balsara=f, c=c, dt=dt)
