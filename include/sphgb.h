@@ -217,6 +217,28 @@ int sph_density(sph_ctx* ctx, const float* m, float* h, float* rho, float* omega
 int sph_force(sph_ctx* ctx, const float* u, const float* vel, float* acc, float* dudt,
               int32_t* count, void* stream);
 
+/* Force with the Monaghan-Balsara artificial viscosity and the time step
+ * (Section 4.1: the viscous terms added to Eq. (dvdt) and Eq. (dudt); Eq. (dt)),
+ * at the h and densities of the last sph_density:
+ *   a_i  = Eq. (dvdt) - 1/4 sum_j m_j Pi_ij (f_i + f_j) (grad W(r,h_i) + grad W(r,h_j)),
+ *   du_i = Eq. (dudt) + 1/8 sum_j m_j Pi_ij (f_i + f_j) v_ij.(grad W(r,h_i) + grad W(r,h_j)),
+ *   Pi_ij = -alpha (c_i + c_j - 3 w_ij) w_ij / (rho_i + rho_j), w_ij = min(0, v_ij.r_ij/r_ij),
+ *   f_i = |div v_i| / (|div v_i| + |curl v_i| + 1e-4 c_i/h_i) (Balsara's switch, with div v
+ *   and curl v summed over r < h_i), c = sqrt(gamma (gamma - 1) u),
+ *   dt_i = c_cfl 2 h_i / max_j (c_i + c_j + max(0, -3 w_ij)),
+ * sums and maximum over r_ij < max(h_i, h_j).
+ *   u        [n] internal energies (caller order, device)
+ *   vel      [3n] velocities, AoS (device; required)
+ *   alpha    viscosity parameter (>= 0; the paper's runs use 0.8)
+ *   c_cfl    CFL constant (> 0; the paper's runs use 1/4)
+ *   acc      [3n] out, accelerations (AoS);  dudt [n] out (nullable);  dt [n] out
+ *   balsara  [n] out, f_i (nullable)
+ * Returns SPH_ERR_NOT_BUILT without a density, SPH_ERR_INVALID_ARG for bad
+ * arguments.  The adjoints do not cover the viscous terms: after this call
+ * sph_force_adjoint and the force part of sph_adjoint need a new sph_force. */
+int sph_force_viscous(sph_ctx* ctx, const float* u, const float* vel, float alpha, float c_cfl,
+                      float* acc, float* dudt, float* dt, float* balsara, void* stream);
+
 /* Reverse mode of the ghost step and the force loop for a scalar L with
  * upstream gradients g_acc = dL/d acc (n x 3) and g_dudt = dL/d dudt
  * (nullable = 0), at the state of the last sph_force:

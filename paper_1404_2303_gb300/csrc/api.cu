@@ -29,6 +29,11 @@ __global__ void k_scatter(long long n, const int* perm, const float* in, float* 
   if (s < n) out[perm[s]] = in[s];
 }
 
+__global__ void k_scatter_z(long long n, const int* perm, const float4* in, float* out) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < n) out[perm[s]] = in[s].z;
+}
+
 __global__ void k_scatter_i(long long n, const int* perm, const int* in, int* out) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s < n) out[perm[s]] = in[s];
@@ -420,7 +425,7 @@ void sph_destroy(sph_ctx* c) {
                  &c->prof_units, &c->solve_ctl, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
                  &c->tmp_b, &c->tmp_c, &c->p_et, &c->nleaf_dev, &c->n_listed, &c->n_ex, &c->n_lo,
                  &c->n_hi, &c->b_lo, &c->b_hi, &c->fl_list, &c->fl_cnt, &c->fl_flag, &c->fl_blk,
-                 &c->fl_over, &c->task_ctl, &c->tree_ctl};
+                 &c->fl_over, &c->task_ctl, &c->tree_ctl, &c->visc4, &c->dt_s};
   for (DBuf* b : all) dbuf_free(*b);
   for (auto& e : c->ev_pending) {
     cudaEventDestroy(e.a);
@@ -637,6 +642,39 @@ int sph_force(sph_ctx* c, const float* u, const float* vel, float* acc, float* d
     c->stats.force_pairs = (int64_t)(tot / 2);
     return read_status(c, s);
   }
+  return SPH_OK;
+}
+
+int sph_force_viscous(sph_ctx* c, const float* u, const float* vel, float alpha, float c_cfl,
+                      float* acc, float* dudt, float* dt, float* balsara, void* stream) {
+  if (!c || !u || !vel || !acc || !dt || !(alpha >= 0.f) || !(c_cfl > 0.f))
+    return SPH_ERR_INVALID_ARG;
+  if (!c->have_density) return SPH_ERR_NOT_BUILT;
+  cudaStream_t s = as_stream(stream);
+  const long long n = c->n;
+  const int* perm = c->perm.as<int>();
+  SPH_TRY(dbuf_ensure(c->visc4, 16 * (size_t)n));
+  SPH_TRY(dbuf_ensure(c->dt_s, 4 * (size_t)n));
+  { k_ghost<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->h.as<float>(), c->pos4.as<float4>(),
+                                         c->rho.as<float>(), c->drho.as<float>(), u, vel,
+                                         c->prm.gamma, c->omega.as<float>(), c->Avec.as<float>(),
+                                         c->u_s.as<float>(), c->vel4.as<float4>(),
+                                         c->fdat.as<float4>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  c->visc_alpha = alpha;
+  c->visc_cfl = c_cfl;
+  SPH_TRY(run_sweep(c, PH_VELDERIV, 0, 0, s));
+  SPH_TRY(run_sweep(c, PH_FORCE_VISC, 0, 0, s));
+  { k_scatter_acc<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->acc4.as<float4>(), acc, dudt); note_launch(); }
+  { k_scatter<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->dt_s.as<float>(), dt); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  if (balsara) {
+    { k_scatter_z<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->visc4.as<float4>(), balsara); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
+  }
+  // the adjoints cover the inviscid force only
+  c->have_force = false;
+  c->fl_valid = false;
   return SPH_OK;
 }
 

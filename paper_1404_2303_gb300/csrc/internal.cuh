@@ -139,6 +139,9 @@ struct sph_ctx {
   // physics state (cell order)
   DBuf rho, drho, nngb, dnngb, d2rho, omega, Avec, fdat;  // fdat: float4 per particle for force
   DBuf d2nngb;    // float d^2 N / dh^2 (h iteration)
+  DBuf visc4;     // float4 (c, rho, Balsara f, div v) for the viscous force
+  DBuf dt_s;      // float time step (Eq. dt)
+  float visc_alpha = 0.f, visc_cfl = 0.25f;
   DBuf vel4;      // float4 (vx, vy, vz, hinv)
   DBuf u_s;       // float
   DBuf acc4;      // float4 (ax, ay, az, dudt)
@@ -221,8 +224,10 @@ enum : int {
   PH_FORCE = 2,        // acc, du/dt (+count)
   PH_FORCE_ADJ = 3,    // force adjoint gather
   PH_DENSITY_ADJ = 4,  // density adjoint gather
-  PH_DUMP_DENSITY = 5,
-  PH_DUMP_FORCE = 6,
+  PH_VELDERIV = 5,     // div v, curl v and the Balsara switch (viscosity)
+  PH_FORCE_VISC = 6,   // force with artificial viscosity and the time-step signal speed
+  PH_DUMP_DENSITY = 8,
+  PH_DUMP_FORCE = 9,
 };
 
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -92,6 +92,12 @@ struct SweepArgs {
   int* queue;
   int* status;
   float delta;
+  float gamma;          // viscosity: adiabatic index, alpha, C_CFL
+  float alpha;
+  float c_cfl;
+  const float* rho_in;  // viscosity: rho and u (cell order), (c, rho, f, div v) per particle
+  const float* u_in;
+  const float4* visc4;
   int kahan;
   int naive;            // ablation: whole targets, no axial window, no box filter
   int bmax;             // largest block (particles)
@@ -133,6 +139,7 @@ struct SweepArgs {
 // ---------------------------------------------------------------------------
 struct PDensity {
   static constexpr int NACC = 5;
+  static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 1;
   static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = false;
@@ -197,6 +204,7 @@ struct PDensity {
 // d^2 rho / dh^2 = sigma/h^5 sum m (12 w + 8 q w' + q^2 w''), w'' = 12 (a - 4b)
 struct PDensityD2 {
   static constexpr int NACC = 1;
+  static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 1;
   static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = false;
@@ -240,6 +248,7 @@ struct PDensityD2 {
 // ---------------------------------------------------------------------------
 struct PForce {
   static constexpr int NACC = 4;
+  static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 3;
   static constexpr bool WRITES = true;  // records the pair lists
   static constexpr bool USES_HJ = true;
@@ -323,6 +332,7 @@ struct PForce {
 // ---------------------------------------------------------------------------
 struct PForceAdj {
   static constexpr int NACC = 6;  // gx, gy, gz, gm, gA, gh
+  static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 4;
   static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = true;
@@ -419,6 +429,7 @@ struct PForceAdj {
 // ---------------------------------------------------------------------------
 struct PDensityAdj {
   static constexpr int NACC = 4;  // gx, gy, gz, gm
+  static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 3;
   static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = true;
@@ -480,11 +491,176 @@ struct PDensityAdj {
 };
 
 // ---------------------------------------------------------------------------
+// velocity divergence and curl (Section 4.1) over r < h_i, with
+// gW = grad W(r, h_i) = (6 sigma/h_i^4)(w'/6)(x_i - x_j)/r:
+//   S_div = sum_j m_j (v_j - v_i) . gW,  S_curl = sum_j m_j (v_j - v_i) x gW,
+// div v_i = S_div/rho_i, curl v_i = -S_curl/rho_i, and the Balsara switch
+// f_i = |div v_i| / (|div v_i| + |curl v_i| + 1e-4 c_i/h_i), c = sqrt(g(g-1)u)
+// ---------------------------------------------------------------------------
+struct PVelDeriv {
+  static constexpr int NACC = 4;  // div, curl x, y, z
+  static constexpr int NMAX = 0;
+  static constexpr int JW = 2;
+  static constexpr bool USES_HJ = false;
+  static constexpr bool WRITES = false;
+  struct I {
+    float x, y, z, vx, vy, vz, h, h2, hinv, G0;
+  };
+  __device__ static void load_i(const SweepArgs& a, int p, I& i) {
+    float4 q = a.pos4[p], v = a.vel4[p];
+    float h = a.h[p];
+    i.x = q.x; i.y = q.y; i.z = q.z;
+    i.vx = v.x; i.vy = v.y; i.vz = v.z;
+    i.hinv = v.w;
+    i.h = h;
+    i.h2 = __fmul_rn(h, h);
+    float hi2 = v.w * v.w;
+    i.G0 = 6.f * SIGMA * hi2 * hi2;
+  }
+  __device__ static void null_i(I& i) {
+    i.x = i.y = i.z = i.vx = i.vy = i.vz = i.h = i.h2 = i.hinv = i.G0 = 0.f;
+  }
+  __device__ static float cut_h(float h, float) { return h; }
+  __device__ static void stage(const SweepArgs& a, int j, unsigned tag, float4 pj, float4* tile, int lane,
+                                int cap) {
+    tile[lane] = pj;
+    tile[cap + lane] = a.vel4[j];
+  }
+  __device__ static bool test(const I& i, const float4* tile, int t, int cap) {
+    float4 p = tile[t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < i.h2;
+  }
+  template <bool COUNT>
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
+    float4 p = tile[t], v = tile[cap + t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
+    float q = r2 * rinv * i.hinv;
+    float aa = fmaxf(1.f - q, 0.f), bb = fmaxf(0.5f - q, 0.f);
+    float g = p.w * i.G0 * fmaf(4.f * bb, bb, -aa * aa) * rinv;  // m_j |gW| / r
+    float ux = v.x - i.vx, uy = v.y - i.vy, uz = v.z - i.vz;   // v_j - v_i
+    acc[0] = fmaf(g, fmaf(uz, dz, fmaf(uy, dy, ux * dx)), acc[0]);
+    acc[1] = fmaf(g, fmaf(uy, dz, -uz * dy), acc[1]);
+    acc[2] = fmaf(g, fmaf(uz, dx, -ux * dz), acc[2]);
+    acc[3] = fmaf(g, fmaf(ux, dy, -uy * dx), acc[3]);
+    if (COUNT) cnt += r2 < i.h2 ? 1 : 0;
+  }
+  __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
+    const float rho = a.rho_in[p];
+    const float div = s[0] / rho;
+    const float cx = -s[1] / rho, cy = -s[2] / rho, cz = -s[3] / rho;
+    const float c = sqrtf(a.gamma * (a.gamma - 1.f) * a.u_in[p]);
+    const float ad = fabsf(div), ac = sqrtf(fmaf(cz, cz, fmaf(cy, cy, cx * cx)));
+    const float f = ad / (ad + ac + 1e-4f * c / a.h[p]);
+    a.o5[p] = make_float4(c, rho, f, div);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// force with the Monaghan-Balsara viscosity of Section 4.1 and the signal
+// speed of Eq. (dt), over r < max(h_i, h_j).  On top of PForce's terms:
+//   a_i  -= 1/4 m_j Pi_ij (f_i + f_j) (G_i + G_j) (x_i - x_j)/r
+//   du_i += 1/8 m_j Pi_ij (f_i + f_j) (G_i + G_j) v_ij.(x_i - x_j)/r
+//   Pi_ij = -alpha (c_i + c_j - 3 w_ij) w_ij / (rho_i + rho_j),
+//   w_ij = min(0, v_ij.(x_i - x_j)/r), G = dW/dr = (6 sigma/h^4)(w'/6),
+// and the largest c_i + c_j + max(0, -3 w_ij) over the pairs with r > 0
+// ---------------------------------------------------------------------------
+struct PForceVisc {
+  static constexpr int NACC = 6;  // a (3), du pressure, du viscous, max signal speed
+  static constexpr int NMAX = 1;
+  static constexpr int JW = 4;
+  static constexpr bool USES_HJ = true;
+  static constexpr bool WRITES = false;
+  struct I {
+    float x, y, z, vx, vy, vz, h, hinv, h2, C, G0, c, rho, f, alpha;
+    int p;
+  };
+  __device__ static void load_i(const SweepArgs& a, int p, I& i) {
+    float4 q = a.pos4[p], v = a.vel4[p], f = a.fdat[p], w = a.visc4[p];
+    i.p = p;
+    i.h = a.h[p];
+    i.x = q.x; i.y = q.y; i.z = q.z;
+    i.vx = v.x; i.vy = v.y; i.vz = v.z;
+    i.hinv = v.w;
+    i.h2 = f.y;
+    i.C = f.z;
+    float hi2 = v.w * v.w;
+    i.G0 = 6.f * SIGMA * hi2 * hi2;
+    i.c = w.x; i.rho = w.y; i.f = w.z;
+    i.alpha = a.alpha;
+  }
+  __device__ static void null_i(I& i) {
+    i.x = i.y = i.z = i.vx = i.vy = i.vz = i.h = i.hinv = i.h2 = i.C = i.G0 = 0.f;
+    i.c = 0.f; i.rho = 1.f; i.f = 0.f; i.alpha = 0.f;
+    i.p = -1;
+  }
+  __device__ static float cut_h(float h, float hj) { return fmaxf(h, hj); }
+  __device__ static void stage(const SweepArgs& a, int j, unsigned tag, float4 pj, float4* tile, int lane,
+                                int cap) {
+    tile[lane] = pj;
+    tile[cap + lane] = a.vel4[j];
+    float4 f = a.fdat[j];
+    tile[2 * cap + lane] = make_float4(f.x, f.y, f.z, __int_as_float(j));
+    tile[3 * cap + lane] = a.visc4[j];
+  }
+  __device__ static bool test(const I& i, const float4* tile, int t, int cap) {
+    float4 p = tile[t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    return r2 < fmaxf(i.h2, tile[2 * cap + t].y);
+  }
+  template <bool COUNT>
+  __device__ static void interact(const I& i, const float4* tile, int t, float* acc, int& cnt, int cap) {
+    float4 p = tile[t], v = tile[cap + t], f = tile[2 * cap + t], w = tile[3 * cap + t];
+    float dx = __fsub_rn(i.x, p.x), dy = __fsub_rn(i.y, p.y), dz = __fsub_rn(i.z, p.z);
+    float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
+    float r = r2 * rinv;
+    float qi = r * i.hinv, qj = r * v.w;
+    float ai = fmaxf(1.f - qi, 0.f), bi = fmaxf(0.5f - qi, 0.f);
+    float aj = fmaxf(1.f - qj, 0.f), bj = fmaxf(0.5f - qj, 0.f);
+    float di = fmaf(4.f * bi, bi, -ai * ai);
+    float dj = fmaf(4.f * bj, bj, -aj * aj);
+    // pressure (as PForce)
+    float tm = p.w * di;
+    float coef = fmaf(tm, i.C, f.x * dj) * rinv;
+    float vx = i.vx - v.x, vy = i.vy - v.y, vz = i.vz - v.z;
+    float vd = fmaf(vz, dz, fmaf(vy, dy, vx * dx));   // v_ij . (x_i - x_j)
+    acc[3] = fmaf(tm * rinv, vd, acc[3]);
+    // viscosity
+    float wv = fminf(0.f, vd * rinv);
+    float Pi = -i.alpha * (i.c + w.x - 3.f * wv) * wv / (i.rho + w.y);
+    float hj2 = v.w * v.w;
+    float gs = fmaf(i.G0, di, 6.f * SIGMA * hj2 * hj2 * dj) * rinv;  // (G_i + G_j)/r
+    float kv = p.w * Pi * (i.f + w.z) * gs;
+    float ct = fmaf(0.25f, kv, coef);
+    acc[0] = fmaf(ct, dx, acc[0]);
+    acc[1] = fmaf(ct, dy, acc[1]);
+    acc[2] = fmaf(ct, dz, acc[2]);
+    acc[4] = fmaf(0.125f * kv, vd, acc[4]);
+    // signal speed of Eq. (dt) over the force pairs (r > 0)
+    const bool pair = r2 > 0.f && r2 < fmaxf(i.h2, f.y);
+    acc[5] = fmaxf(acc[5], pair ? i.c + w.x + fmaxf(0.f, -3.f * vd * rinv) : 0.f);
+    if (COUNT) cnt += (r2 < fmaxf(i.h2, f.y) && __float_as_int(f.w) != i.p) ? 1 : 0;
+  }
+  __device__ static void finalize(const SweepArgs& a, int p, const float* s) {
+    const float C = a.fdat[p].z;
+    a.o4[p] = make_float4(-s[0], -s[1], -s[2], fmaf(C, s[3], s[4]));
+    const float c = a.visc4[p].x;
+    const float sig = s[5] > 0.f ? s[5] : 2.f * c;
+    a.o0[p] = a.c_cfl * 2.f * a.h[p] / sig;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // pair dump (test hook): records accepted pairs in caller indices
 // ---------------------------------------------------------------------------
 template <int FORCE>
 struct PDump {
   static constexpr int NACC = 1;
+  static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 2;
   static constexpr bool WRITES = false;
   static constexpr bool USES_HJ = FORCE != 0;
@@ -547,7 +723,9 @@ __device__ __forceinline__ void fold(float* acc, float* cmp, float* part, int ka
 #pragma unroll
   for (int k = 0; k < P::NACC; ++k) {
     float x = part[k];
-    if (kahan) {
+    if (k >= P::NACC - P::NMAX) {  // a running maximum (partials start at 0)
+      acc[k] = fmaxf(acc[k], x);
+    } else if (kahan) {
       float S = acc[k];
       float T = S + x;
       cmp[k] += fabsf(S) >= fabsf(x) ? (S - T) + x : (x - T) + S;
@@ -1016,8 +1194,8 @@ template <class P, bool COUNT>
 int launch(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
   a.cap = c->sweep_cap;
   a.bmax = c->prm.block_max;
-  const bool list = a.cap <= 256 && (a.fl_list != nullptr ||
-                                     (c->cur_phase < PH_DUMP_DENSITY &&
+  const bool list = a.cap <= 256 && (a.fl_list != nullptr || c->cur_phase == PH_FORCE_VISC ||
+                                     (c->cur_phase <= PH_DENSITY_ADJ &&
                                       ((c->prm.sweep_lists >> c->cur_phase) & 1)));
   return list ? launch_shape<P, COUNT, true>(c, a, s) : launch_shape<P, COUNT, false>(c, a, s);
 }
@@ -1095,7 +1273,7 @@ int set_dir_table(sph_ctx* c) {
 int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t s) {
   if (c->nblock == 0) return SPH_OK;
   c->cur_phase = phase;
-  if (c->profile && phase < PH_DUMP_DENSITY) counting = 1;
+  if (c->profile && phase != PH_DUMP_DENSITY && phase != PH_DUMP_FORCE) counting = 1;
   SPH_TRY(set_dir_table(c));
   SweepArgs a{};
   a.nblock = c->nblock;
@@ -1180,6 +1358,19 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
       a.o4 = c->g_x4.as<float4>();
       return counting ? launch_pairs<PDensityAdj, true>(c, a, s)
                       : launch_pairs<PDensityAdj, false>(c, a, s);
+    case PH_VELDERIV:
+      a.rho_in = c->rho.as<float>();
+      a.u_in = c->u_s.as<float>();
+      a.gamma = c->prm.gamma;
+      a.o5 = c->visc4.as<float4>();
+      return counting ? launch<PVelDeriv, true>(c, a, s) : launch<PVelDeriv, false>(c, a, s);
+    case PH_FORCE_VISC:
+      a.visc4 = c->visc4.as<float4>();
+      a.alpha = c->visc_alpha;
+      a.c_cfl = c->visc_cfl;
+      a.o4 = c->acc4.as<float4>();
+      a.o0 = c->dt_s.as<float>();
+      return counting ? launch<PForceVisc, true>(c, a, s) : launch<PForceVisc, false>(c, a, s);
     case PH_DUMP_DENSITY:
     case PH_DUMP_FORCE:
       a.perm = c->perm.as<int>();

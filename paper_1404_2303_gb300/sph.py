@@ -138,6 +138,19 @@ class SPH:
                                  _stream()), "sph_force")
         return acc, dudt, cnt
 
+    def force_viscous(self, u, vel, alpha=0.8, c_cfl=0.25):
+        """Force with the Monaghan-Balsara viscosity and the time step of
+        Eq. (dt): returns (acc, dudt, dt, balsara).  No adjoint."""
+        u = _f32(u)
+        vel = _f32(vel, (self.n, 3))
+        acc = torch.empty((self.n, 3), device=u.device, dtype=torch.float32)
+        z = lambda: torch.empty(self.n, device=u.device, dtype=torch.float32)
+        dudt, dt, f = z(), z(), z()
+        check(self.lib.sph_force_viscous(self.h, _ptr(u), _ptr(vel), float(alpha), float(c_cfl),
+                                         _ptr(acc), _ptr(dudt), _ptr(dt), _ptr(f), _stream()),
+              "sph_force_viscous")
+        return acc, dudt, dt, f
+
     # -- adjoints ------------------------------------------------------------
     def force_adjoint(self, g_acc, g_dudt=None):
         g_acc = _f32(g_acc, (self.n, 3))

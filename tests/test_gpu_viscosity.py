@@ -1,0 +1,93 @@
+"""GPU parity of the force with the Monaghan-Balsara viscosity and of the
+time step of Eq. (dt) (Section 4.1) against the FP64 oracle, through the
+C ABI (sph_force_viscous).  Tolerances as for the inviscid force: 1e-4 of
+the rms for accelerations and du/dt; the switch and the time step (a
+maximum over pairs, which can change where the FP32 and FP64 neighbour
+tests straddle r = h) per particle at the 99.9th percentile."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sph_oracle as O
+import synth.configs as C
+
+pytestmark = pytest.mark.gpu
+ALPHA, CCFL = 0.8, 0.25
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _rms_err(a, ref):
+    rms = np.sqrt(np.mean(np.sum(ref ** 2, axis=1)))
+    return np.max(np.linalg.norm(a - ref, axis=1)) / rms
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_1404_2303_gb300 import SPH
+    d = C.random_box(20000, 13, "clumped", v_sigma=0.3)
+    s = SPH()
+    s.build(_t(d["x"]))
+    s.density(_t(d["m"]))
+    ref = O.evaluate(d["x"], d["m"], d["u"], v=d["v"], h_guess=0.1)
+    vis = O.evaluate_viscosity(ref, d["x"], d["m"], d["u"], d["v"], ALPHA, CCFL)
+    return d, s, ref, vis
+
+
+def test_viscous_force_switch_and_time_step_match_the_oracle(case):
+    d, s, ref, vis = case
+    acc, dudt, dt, f = s.force_viscous(_t(d["u"]), _t(d["v"]), ALPHA, CCFL)
+    a = acc.cpu().numpy().astype(np.float64)
+    du = dudt.cpu().numpy().astype(np.float64)
+    a_ref = ref["a"] + vis["a_visc"]
+    du_ref = ref["dudt"] + vis["dudt_visc"]
+    assert np.abs(vis["a_visc"]).max() > 0.01 * np.abs(ref["a"]).max()   # viscosity matters here
+    assert _rms_err(a, a_ref) <= 1e-4
+    assert np.max(np.abs(du - du_ref)) / np.sqrt(np.mean(du_ref ** 2)) <= 1e-4
+    fe = np.abs(f.cpu().numpy().astype(np.float64) - vis["balsara"])
+    assert np.quantile(fe, 0.999) <= 1e-4 and fe.max() <= 1e-2
+    te = np.abs(dt.cpu().numpy().astype(np.float64) / vis["dt"] - 1.0)
+    assert np.quantile(te, 0.999) <= 1e-4 and te.max() <= 5e-2
+    # exact conservation of the pairwise terms, to FP32 summation
+    m = d["m"].astype(np.float64)
+    ma = m[:, None] * a
+    assert np.abs(ma.sum(0)).max() <= 1e-5 * np.abs(ma).sum()
+    v = d["v"].astype(np.float64)
+    e = m * (du + np.einsum("ij,ij->i", v, a))
+    assert abs(e.sum()) <= 1e-4 * np.abs(e).sum()
+
+
+def test_zero_viscosity_is_the_inviscid_force(case):
+    d, s, ref, vis = case
+    acc0, du0, dt0, _ = s.force_viscous(_t(d["u"]), _t(d["v"]), 0.0, CCFL)
+    acc, du, _ = s.force(_t(d["u"]), _t(d["v"]))
+    a0, a1 = acc0.cpu().numpy(), acc.cpu().numpy()
+    assert _rms_err(a0.astype(np.float64), a1.astype(np.float64)) <= 1e-6
+    d0, d1 = du0.cpu().numpy().astype(np.float64), du.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(d0 - d1)) <= 1e-6 * np.sqrt(np.mean(d1 ** 2))
+    # the time step does not depend on alpha
+    te = np.abs(dt0.cpu().numpy().astype(np.float64) / vis["dt"] - 1.0)
+    assert np.quantile(te, 0.999) <= 1e-4
+
+
+def test_viscous_force_needs_a_density_and_velocities():
+    from paper_1404_2303_gb300 import SPH
+    from paper_1404_2303_gb300._lib import SphError
+    d = C.random_box(2000, 3, "uniform", v_sigma=0.1)
+    s = SPH()
+    s.build(_t(d["x"]))
+    with pytest.raises(SphError) as e:
+        s.force_viscous(_t(d["u"]), _t(d["v"]))
+    assert e.value.code == -6
+    s.density(_t(d["m"]))
+    with pytest.raises(SphError) as e:
+        s.force_viscous(_t(d["u"]), _t(d["v"]), alpha=-1.0)
+    assert e.value.code == -1
