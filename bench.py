@@ -454,6 +454,24 @@ def main():
             sa.close()
         ablation["sorting_speedup"] = {
             k: ablation["naive"][k] / ablation["sorted"][k] for k in ("density_ms", "force_ms")}
+    # ---- next row: the force with artificial viscosity and the Eq. (dt) time
+    # step (Section 4.1) on the same workload: the velocity-derivative sweep
+    # and the viscous force sweep, three calls at the solved h
+    viscous = None
+    if not args.no_ablation:
+        sph.density(m)
+        sph.force_viscous(u, vel)
+        torch.cuda.synchronize()
+        sph.profile(True)
+        for _ in range(3):
+            sph.force_viscous(u, vel)
+        torch.cuda.synchronize()
+        vst = sph.stats()
+        sph.profile(False)
+        viscous = {"velocity_derivatives_ms": vst["sweep_ms"][5] / 3,
+                   "viscous_force_ms": vst["sweep_ms"][6] / 3,
+                   "force_pairs_per_s": vst["sweep_units"][6] / 2 / (vst["sweep_ms"][6] / 1e3),
+                   "kernels": ["k_sweep<PVelDeriv>", "k_sweep<PForceVisc>"]}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -495,6 +513,7 @@ def main():
                                                             "rebuilds")},
             "h_iteration_active": [x for x in prod["stats"]["newton_active"] if x],
             "ablation_naive_vs_sorted": ablation,
+            "viscous_force": viscous,
             "build_stages_ms": {BUILD_STAGES[k]: st["build_ms"][k] / args.steps for k in range(8)},
             "cpu_baseline": cpu,
         }
