@@ -896,10 +896,10 @@ __global__ void k_box_hmax(long long n, const long long* off, int nbox, const fl
   if (lane == __ffs(peers) - 1 && b >= 0) atomicMax(&out[b], mx);
 }
 
-// ---------------------------------------------------------------- flat merge
-// Elements of every (node, needed direction) of one generation form one flat
-// index space; each thread ranks one element of one sub-list (child cell or
-// leaf block) against the node's other sub-lists by binary search.
+// ---------------------------------------------------------------- merges
+// A listed node's sorted list of a needed direction is the merge of its
+// sub-lists (its children's lists, or its blocks' lists for a leaf): one CTA
+// per (node, direction) ranks every element against the other sub-lists.
 __device__ __forceinline__ bool mergeable(int node, const int* need, const int* child0,
                                           const int* nblk, const int* count, const int* listed) {
   return need[node] != 0 && count[node] > 0 && listed[node] && !(child0[node] < 0 && nblk[node] <= 1);
