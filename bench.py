@@ -172,7 +172,8 @@ def oracle_sample_rate(d, seconds_target=15.0, seed=0, sample=None):
     r = O.evaluate_sample(x, m, u, idx, v=v)
     dt = time.perf_counter() - t0
     units = float(np.sum(r["count"]) + 0.5 * np.sum(r["force_count"]))
-    return dict(value=units / dt, seconds=dt, sample=int(S), units=units)
+    base = int(d["offsets"][b]) if "offsets" in d else 0
+    return dict(value=units / dt, seconds=dt, sample=int(S), units=units, ref=r, index=base + idx)
 
 
 def max_over_ranks(x, device=None):
@@ -473,6 +474,7 @@ def main():
                    "force_pairs_per_s": vst["sweep_units"][6] / 2 / (vst["sweep_ms"][6] / 1e3),
                    "kernels": ["k_sweep<PVelDeriv>", "k_sweep<PForceVisc>"]}
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
             r = oracle_sample_rate(d, sample=args.ref_sample)
@@ -480,6 +482,21 @@ def main():
                    "sample": f"{r['sample']} random particles of {args.workload}, evaluated from "
                              f"scratch in {r['seconds']:.1f} s (h solve of the sample and its "
                              "force partners, density, force)"}
+            # the oracle's values of that sample against this run's results
+            try:
+                gi, ref = r["index"], r["ref"]
+                gh = den["h"].double().cpu().numpy()[gi]
+                grho = den["rho"].double().cpu().numpy()[gi]
+                ga = acc.double().cpu().numpy()[gi]
+                arms = float(np.sqrt(np.mean(np.sum(ref["a"] ** 2, axis=1))))
+                parity = {"particles": int(len(gi)),
+                          "max_rel_err_h": float(np.max(np.abs(gh / ref["h"] - 1.0))),
+                          "max_rel_err_rho": float(np.max(np.abs(grho / ref["rho"] - 1.0))),
+                          "max_err_acc_over_rms": float(np.max(np.linalg.norm(ga - ref["a"], axis=1))
+                                                        / arms) if arms > 0 else None,
+                          "tolerances": {"h": 1e-5, "rho": 1e-5, "acc": 1e-4}}
+            except Exception as e:  # noqa: BLE001
+                parity = {"failed": str(e)}
         except Exception as e:  # noqa: BLE001
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {e}"}
@@ -514,6 +531,7 @@ def main():
             "h_iteration_active": [x for x in prod["stats"]["newton_active"] if x],
             "ablation_naive_vs_sorted": ablation,
             "viscous_force": viscous,
+            "sampled_parity": parity,
             "build_stages_ms": {BUILD_STAGES[k]: st["build_ms"][k] / args.steps for k in range(8)},
             "cpu_baseline": cpu,
         }
