@@ -213,7 +213,10 @@ int sph_density(sph_ctx* ctx, const float* m, float* h, float* rho, float* omega
  *   dudt   out (nullable): du_i/dt
  *   count  out (nullable, int32): partners j != i with r_ij < max(h_i,h_j)
  *          (FP32 predicate); when given the call synchronises and records
- *          the number of unordered pairs in sph_stats.force_pairs */
+ *          the number of unordered pairs in sph_stats.force_pairs
+ * With pair_list_cap > 0 the sweep also records every particle's pairs
+ * (context-owned, 4 n pair_list_cap bytes) for the adjoint calls that
+ * follow. */
 int sph_force(sph_ctx* ctx, const float* u, const float* vel, float* acc, float* dudt,
               int32_t* count, void* stream);
 
@@ -276,9 +279,12 @@ int sph_pairs_dump(sph_ctx* ctx, int32_t phase, int64_t cap, int32_t* pi, int32_
                    int64_t* n_out, void* stream);
 
 /* Enable (1) or disable (0) per-launch timing of the sweep kernels with
- * CUDA events recorded on the launch stream (no synchronisation is added);
- * either call resets the accumulated times.  sph_get_stats synchronises on
- * the recorded events and reports per-phase totals. */
+ * CUDA events recorded on the launch stream (no synchronisation is added),
+ * counting variants of the sweeps (accepted pairs and candidates), the h
+ * iteration as a host loop, and timing of the build stages (there the
+ * stream is synchronised at each stage boundary); either call resets the
+ * accumulated values.  sph_get_stats synchronises on the recorded events
+ * and reports per-phase totals. */
 int sph_profile(sph_ctx* ctx, int32_t enable);
 
 /* Change the sweep launch shape of a built context (the decomposition is
