@@ -8,8 +8,13 @@ solve, ghost, force, and the adjoint of L = sum (rho - 1)^2 + sum |a|^2.
 Units per step = directed density interactions (r < h_i, self included) +
 unordered force pairs (r < max(h_i, h_j)), both at the solved h.
 
-Default workload: 128^3 multi-resolution box (jittered lattice with 20 %
-of sites removed + Plummer clump holding 20 % of the particles).
+Default workload: the large clustered box, 256^3 particles drawn from a
+lognormal density field (h spans ~1300x), the largest single-GPU
+configuration.  The line also carries the plain-FP32 forward (no
+compensated sums) on the same GPU, a small full-oracle parity check with
+per-quantity errors (h, rho, a, du/dt, and the three gradients), short
+timings of the other workloads, the naive-versus-sorted ablation and the
+viscous force (both on the 128^3 multi-resolution box).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -45,8 +50,7 @@ PHASE_KERNELS = {0: "k_sweep<PDensity>", 1: "k_listeval<PDensityD2>", 2: "k_swee
 BUILD_STAGES = ["morton_order", "h_estimate", "octree", "pair_tasks", "blocks_and_block_sorts",
                 "list_merge", "interaction_lists", "node_h_max"]
 PHASE_NAMES = {0: "density", 1: "density_d2", 2: "force", 3: "force_adjoint", 4: "density_adjoint"}
-SMS = 152
-LANES = 128
+LANES = 128  # FP32 lanes per SM (four sub-partitions of 32)
 
 
 def workload(name):
@@ -225,21 +229,149 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _t(a, dev, dtype=None):
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    return t.to(dtype) if dtype is not None else t
+
+
+def _step_fn(sph, d, stream, ev=None, adjoint=True):
+    """One step of the path on workload d through the public API; with ev,
+    CUDA events on the launch stream mark the forward / adjoint split."""
+    import torch
+    batched = "offsets" in d
+
+    def step(pos, m, u, vel):
+        if ev is not None:
+            ev.setdefault("f0", []).append(torch.cuda.Event(enable_timing=True))
+            ev["f0"][-1].record(stream)
+        if batched:
+            sph.build_batch(pos, d["offsets"], d["boxes"])
+        else:
+            sph.build(pos)
+        den = sph.density(m)
+        acc, dudt, _ = sph.force(u, vel)
+        if ev is not None:
+            ev.setdefault("f1", []).append(torch.cuda.Event(enable_timing=True))
+            ev["f1"][-1].record(stream)
+        if not adjoint:
+            return den, acc, dudt, None, None, None
+        g_pos, g_m, g_u = sph.adjoint(2.0 * (den["rho"] - 1.0), 2.0 * acc, None)
+        if ev is not None:
+            ev.setdefault("a1", []).append(torch.cuda.Event(enable_timing=True))
+            ev["a1"][-1].record(stream)
+        return den, acc, dudt, g_pos, g_m, g_u
+    return step
+
+
+def _count_units(sph, m, u, vel, h):
+    sph.density_fixed_h(m, h, count=True)
+    sph.force(u, vel, count=True)
+    st = sph.stats()
+    return st["density_interactions"], st["force_pairs"]
+
+
+def other_workload(name, dev, params, warmup=2, steps=3):
+    """Short timing of another configuration: full steps (build, density with
+    the h solve, force, adjoint) between device events."""
+    import torch
+    from paper_1404_2303_gb300 import SPH
+    d = workload(name)
+    pos, m = _t(d["x"], dev, torch.float64), _t(d["m"], dev)
+    u, vel = _t(d["u"], dev), _t(d["v"], dev)
+    sph = SPH(**params)
+    stream = torch.cuda.current_stream()
+    step = _step_fn(sph, d, stream)
+    for _ in range(warmup):
+        out = step(pos, m, u, vel)
+    torch.cuda.synchronize()
+    dens, fp = _count_units(sph, m, u, vel, out[0]["h"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step(pos, m, u, vel)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = sph.stats()
+    sph.close()
+    return {"particles": int(d["x"].shape[0]), "ms_per_step": ms, "value": (dens + fp) / (ms / 1e3),
+            "units_per_step": int(dens + fp), "newton_iters": st["newton_iters"],
+            "rebuilds": st["rebuilds"], "steps": steps}
+
+
+def small_parity(dev, n=4096, seed=29):
+    """Full-oracle parity of one small clumped box with random velocities:
+    per-quantity errors of h, rho, a, du/dt and of the gradients of
+    L = sum (rho - 1)^2 + sum |a|^2 + sum w du/dt."""
+    import torch
+    from oracle import sph_oracle as O
+    from paper_1404_2303_gb300 import SPH
+    import synth.configs as C
+    d = C.random_box(n, seed, "clumped", v_sigma=0.1)
+    sph = SPH()
+    sph.build(_t(d["x"], dev, torch.float64))
+    den = sph.density(_t(d["m"], dev))
+    acc, dudt, _ = sph.force(_t(d["u"], dev), _t(d["v"], dev))
+    w = np.random.default_rng(3).normal(size=n).astype(np.float32)
+    g = sph.adjoint(2.0 * (den["rho"] - 1.0), 2.0 * acc, _t(w, dev))
+    torch.cuda.synchronize()
+    ref = O.evaluate(d["x"], d["m"], d["u"], v=d["v"], h_guess=0.1)
+    f64 = lambda t: t.double().cpu().numpy()
+    gref = O.gradient(ref, d["x"], d["m"], d["u"], d["v"].astype(np.float64),
+                      2.0 * (f64(den["rho"]) - 1.0), 2.0 * f64(acc), w.astype(np.float64))
+    rms = lambda a: float(np.sqrt(np.mean(np.sum(np.atleast_2d(a.T).T ** 2, axis=-1)))) \
+        if a.ndim > 1 else float(np.sqrt(np.mean(a ** 2)))
+    out = {"particles": n, "config": "uniform + Gaussian clumps, velocities N(0, 0.1^2)",
+           "max_rel_err_h": float(np.max(np.abs(f64(den["h"]) / ref["h"] - 1))),
+           "max_rel_err_rho": float(np.max(np.abs(f64(den["rho"]) / ref["rho"] - 1))),
+           "max_err_acc_over_rms": float(np.max(np.linalg.norm(f64(acc) - ref["a"], axis=1))
+                                         / rms(ref["a"])),
+           "max_err_dudt_over_rms": float(np.max(np.abs(f64(dudt) - ref["dudt"])) / rms(ref["dudt"]))}
+    for name, got, want in (("x", g[0], gref["g_x"]), ("m", g[1], gref["g_m"]), ("u", g[2], gref["g_u"])):
+        gg = f64(got).reshape(want.shape)
+        r = float(np.sqrt(np.mean(want ** 2)))
+        out[f"grad_{name}_rel_l2"] = float(np.linalg.norm(gg - want) / np.linalg.norm(want))
+        out[f"grad_{name}_max_elem"] = float(np.max(np.abs(gg - want) / (r + np.abs(want))))
+    out["tolerances"] = {"h": 1e-5, "rho": 1e-5, "acc": 1e-4, "dudt": 1e-4, "grad_rel_l2": 1e-3,
+                         "grad_elem": 1e-3}
+    sph.close()
+    return out
+
+
+def oracle_full_rate():
+    """The oracle on the whole 16^3 jittered lattice (all host cores): units
+    (directed density interactions + unordered force pairs) per second."""
+    from oracle import sph_oracle as O
+    import synth.configs as C
+    d = C.uniform_lattice(16, seed=1)
+    t0 = time.perf_counter()
+    f = O.evaluate(d["x"], d["m"], d["u"], h_guess=d["h_guess"])
+    dt = time.perf_counter() - t0
+    units = float(f["count"].sum() + 0.5 * f["force_count"].sum())
+    return {"value": units / dt, "seconds": dt, "units": units,
+            "sample": "the whole 16^3 jittered lattice (4096 particles), tree build included"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="multires128")
+    ap.add_argument("--workload", default="lognormal256")
+    ap.add_argument("--side-workload", default="multires128",
+                    help="workload of the naive-versus-sorted ablation and the viscous force")
+    ap.add_argument("--others", default="multires128,batch64,sinusoid64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--kahan", type=int, default=1)
     ap.add_argument("--block-max", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--no-ablation", action="store_true",
-                    help="skip the naive-versus-sorted sweep comparison")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ablation, the viscous force, the other workloads and the small "
+                         "full-oracle parity check")
     ap.add_argument("--profile-step", action="store_true",
                     help="for kernel profilers: run --warmup steps, then one step with the h "
                          "iteration as a host loop (every sweep a separate launch), and exit")
@@ -264,31 +396,23 @@ def main():
     n = d["x"].shape[0]
     dev = torch.device("cuda", local)
     # inputs resident in HBM
-    pos = torch.tensor(d["x"], device=dev, dtype=torch.float64)
-    m = torch.tensor(d["m"], device=dev)
-    u = torch.tensor(d["u"], device=dev)
-    vel = torch.tensor(d["v"], device=dev)
+    pos = _t(d["x"], dev, torch.float64)
+    m, u, vel = _t(d["m"], dev), _t(d["u"], dev), _t(d["v"], dev)
     params = {"kahan": args.kahan}
     if args.block_max:
         params["block_max"] = args.block_max
     if args.warps:
         params["warps_per_cta"] = args.warps
+    stream = torch.cuda.current_stream()
     if args.profile_step:
         sp = SPH(use_graph=0, **params)
+        step = _step_fn(sp, d, stream)
         for _ in range(args.warmup + 1):
-            if "offsets" in d:
-                sp.build_batch(pos, d["offsets"], d["boxes"])
-            else:
-                sp.build(pos)
-            den = sp.density(m)
-            acc, _, _ = sp.force(u, vel)
-            sp.adjoint(2.0 * (den["rho"] - 1.0), 2.0 * acc, None)
+            den = step(pos, m, u, vel)[0]
         torch.cuda.synchronize()
         print(json.dumps({"profile_step": args.workload, "iters": den["iters"]}), flush=True)
         return 0
     sph = SPH(**params)
-    stream = torch.cuda.current_stream()
-    batched = "offsets" in d
 
     # sweep launch shape from the project's autotuner, timed on this workload
     tuned = None
@@ -298,40 +422,22 @@ def main():
                               use_cache=False, **params)
         sph.set_sweep_config(**shape)
         tuned = {"shape": shape, "candidates": len(timings)}
+    else:
+        shape = None
 
     ev = {}
-
-    def step(pos, m, u, vel, mark=False):
-        if mark:
-            ev.setdefault("f0", []).append(torch.cuda.Event(enable_timing=True))
-            ev["f0"][-1].record(stream)
-        if batched:
-            sph.build_batch(pos, d["offsets"], d["boxes"])
-        else:
-            sph.build(pos)
-        den = sph.density(m)
-        acc, dudt, _ = sph.force(u, vel)
-        if mark:
-            ev.setdefault("f1", []).append(torch.cuda.Event(enable_timing=True))
-            ev["f1"][-1].record(stream)
-        g_pos, g_m, g_u = sph.adjoint(2.0 * (den["rho"] - 1.0), 2.0 * acc, None)
-        if mark:
-            ev.setdefault("a1", []).append(torch.cuda.Event(enable_timing=True))
-            ev["a1"][-1].record(stream)
-        return den, acc, dudt, g_pos, g_m, g_u
-
+    step = _step_fn(sph, d, stream, ev)
     for _ in range(args.warmup):
         out = step(pos, m, u, vel)
+    ev.clear()
     torch.cuda.synchronize()
     # units per step (counted at the solved h, outside the timed region)
     den = out[0]
-    sph.density_fixed_h(m, den["h"], count=True)
-    sph.force(u, vel, count=True)
-    st = sph.stats()
-    units = st["density_interactions"] + st["force_pairs"]
+    dens_units, force_units = _count_units(sph, m, u, vel, den["h"])
+    units = dens_units + force_units
 
-    def timed(profile):
-        """K full steps between a barrier + synchronize on both sides."""
+    def timed(profile, steps):
+        """steps full steps between a barrier + synchronize on both sides."""
         ev.clear()
         sph.profile(profile)
         launches0 = sph.launch_count()
@@ -343,30 +449,51 @@ def main():
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        for _ in range(args.steps):
-            step(pos, m, u, vel, mark=True)
+        for _ in range(steps):
+            step(pos, m, u, vel)
         t1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         clocks = clk.stop()
         launches = sph.launch_count() - launches0
-        ms = t0.elapsed_time(t1) / args.steps
+        ms = t0.elapsed_time(t1) / steps
         fwd = float(np.mean([a.elapsed_time(b) for a, b in zip(ev["f0"], ev["f1"])]))
         adj = float(np.mean([a.elapsed_time(b) for a, b in zip(ev["f1"], ev["a1"])]))
         stats = sph.stats()
         sph.profile(False)
         ms = max_over_ranks(ms, dev)
-        return dict(ms=ms, fwd=fwd, adj=adj, launches=launches, stats=stats, clocks=clocks)
+        return dict(ms=ms, fwd=fwd, adj=adj, launches=launches, stats=stats, clocks=clocks,
+                    steps=steps)
 
     # production pass: device-side graphs for the h iteration, no profiling
-    prod = timed(False)
+    prod = timed(False, args.steps)
     # profiled pass: every sweep launch bracketed by CUDA events on its stream
-    prof = timed(True)
+    prof = timed(True, max(1, min(args.steps, 3)))
     ms, fwd_ms, adj_ms, launches, clocks = (prod["ms"], prod["fwd"], prod["adj"], prod["launches"],
                                             prod["clocks"])
     st = prof["stats"]
     value = job_rate(units, world, ms)
+
+    # ---- the plain-FP32 forward (no compensated sums) on the same GPU
+    sp32 = SPH(**dict(params, kahan=0))
+    if shape:
+        sp32.set_sweep_config(**shape)
+    step32 = _step_fn(sp32, d, stream, adjoint=False)
+    step32(pos, m, u, vel)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out32 = step32(pos, m, u, vel)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd32_ms = e0.elapsed_time(e1) / args.steps
+    rho_k, rho_p = den["rho"].double(), out32[0]["rho"].double()
+    plain32 = {"fwd_ms": fwd32_ms, "value": units / (fwd32_ms / 1e3),
+               "compensated_fwd_ms": fwd_ms,
+               "max_rel_diff_rho_vs_compensated": float(((rho_p - rho_k).abs() / rho_k).max())}
+    sp32.close()
 
     # ---- end to end through the public API: pinned host inputs, host outputs
     hpos = torch.tensor(d["x"], dtype=torch.float64).pin_memory()
@@ -379,14 +506,16 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    step_e2e = _step_fn(sph, d, stream)
     e0.record(stream)
     for _ in range(args.steps):
         dp = hpos.to(dev, non_blocking=True)
         dm = hm.to(dev, non_blocking=True)
         du_ = hu.to(dev, non_blocking=True)
         dv = hv.to(dev, non_blocking=True)
-        den, acc, dudt, g_pos, g_m, g_u = step(dp, dm, du_, dv)
-        outs_host = [t.to("cpu", non_blocking=True) for t in (den["rho"], den["h"], acc, dudt, g_pos, g_m, g_u)]
+        den2, acc, dudt, g_pos, g_m, g_u = step_e2e(dp, dm, du_, dv)
+        outs_host = [t.to("cpu", non_blocking=True)
+                     for t in (den2["rho"], den2["h"], acc, dudt, g_pos, g_m, g_u)]
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -398,7 +527,8 @@ def main():
     # ---- roofline of the dominant sweep kernel
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    peak_alu = SMS * LANES * sm_max * 1e6  # FP32 lane-instructions/s at the maximum SM clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_alu = sms * LANES * sm_max * 1e6  # FP32 lane-instructions/s at the maximum SM clock
     phase_ms = st["sweep_ms"]
     dom = int(np.argmax(phase_ms[:5]))
     kernels = {}
@@ -411,9 +541,10 @@ def main():
             u_ph = u_ph / 2.0  # ordered -> unordered pairs
         kernels[PHASE_NAMES[ph]] = {
             "kernel": PHASE_KERNELS[ph],
-            "launches_per_step": L / args.steps, "ms_per_launch": phase_ms[ph] / L,
+            "launches_per_step": L / prof["steps"], "ms_per_launch": phase_ms[ph] / L,
             "units_per_launch": u_ph / L,
-            "share_of_step": phase_ms[ph] / args.steps / prof["ms"],
+            "share_of_step": phase_ms[ph] / prof["steps"] / prof["ms"],
+            "frac_fp32": (u_ph / L) * INSTR[ph] / (phase_ms[ph] / L / 1e3) / peak_alu,
         }
     roof = None
     dname = PHASE_NAMES[dom]
@@ -423,28 +554,38 @@ def main():
         roof = {"kernel": PHASE_KERNELS[dom], "bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak_alu / 1e12, "unit": "T FP32-instr/s",
                 "frac": achieved / peak_alu, "traffic": profiled_traffic(dname),
-                "peak_source": f"{SMS} SMs x {LANES} FP32 lanes x {sm_max:.0f} MHz "
-                               f"(sm_max_mhz of {pk_kind} peaks)",
+                "peak_source": f"{sms} SMs (device attribute) x {LANES} FP32 lanes x "
+                               f"{sm_max:.0f} MHz (sm_max_mhz of {pk_kind} peaks)",
                 "instr_per_unit": INSTR[dom]}
-    # ---- ablation of the sorting (Section 3.3): the naive cell-pair loop over
-    # the same tasks, one density and one force sweep at the solved h each
-    ablation = None
-    if not args.no_ablation:
-        ablation = {}
-        h_sol = den["h"]
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        side = workload(args.side_workload)
+        spos = _t(side["x"], dev, torch.float64)
+        sm_, su, sv = _t(side["m"], dev), _t(side["u"], dev), _t(side["v"], dev)
+        sb = "offsets" in side
+        hs = SPH(**params)
+        if sb:
+            hs.build_batch(spos, side["offsets"], side["boxes"])
+        else:
+            hs.build(spos)
+        h_sol = hs.density(sm_)["h"]
+        # ---- ablation of the sorting (Section 3.3): the naive cell-pair loop
+        # over the same tasks, one density and one force sweep at the solved h
+        ablation = {"workload": args.side_workload}
         for mode, name in ((1, "sorted"), (0, "naive")):
             sa = SPH(sorted_sweep=mode, pair_list_cap=0, **params)
-            if batched:
-                sa.build_batch(pos, d["offsets"], d["boxes"], h_guess=h_sol)
+            if sb:
+                sa.build_batch(spos, side["offsets"], side["boxes"], h_guess=h_sol)
             else:
-                sa.build(pos, h_guess=h_sol)
-            sa.density_fixed_h(m, h_sol)
-            sa.force(u, vel)
+                sa.build(spos, h_guess=h_sol)
+            sa.density_fixed_h(sm_, h_sol)
+            sa.force(su, sv)
             torch.cuda.synchronize()
             sa.profile(True)
             for _ in range(3):
-                sa.density_fixed_h(m, h_sol)
-                sa.force(u, vel)
+                sa.density_fixed_h(sm_, h_sol)
+                sa.force(su, sv)
             torch.cuda.synchronize()
             sst = sa.stats()
             sa.profile(False)
@@ -455,24 +596,38 @@ def main():
             sa.close()
         ablation["sorting_speedup"] = {
             k: ablation["naive"][k] / ablation["sorted"][k] for k in ("density_ms", "force_ms")}
-    # ---- next row: the force with artificial viscosity and the Eq. (dt) time
-    # step (Section 4.1) on the same workload: the velocity-derivative sweep
-    # and the viscous force sweep, three calls at the solved h
-    viscous = None
-    if not args.no_ablation:
-        sph.density(m)
-        sph.force_viscous(u, vel)
+        extras["ablation_naive_vs_sorted"] = ablation
+        # ---- next row: the force with artificial viscosity and the Eq. (dt)
+        # time step (Section 4.1): velocity-derivative and viscous force sweeps
+        hs.force_viscous(su, sv)
         torch.cuda.synchronize()
-        sph.profile(True)
+        hs.profile(True)
         for _ in range(3):
-            sph.force_viscous(u, vel)
+            hs.force_viscous(su, sv)
         torch.cuda.synchronize()
-        vst = sph.stats()
-        sph.profile(False)
-        viscous = {"velocity_derivatives_ms": vst["sweep_ms"][5] / 3,
-                   "viscous_force_ms": vst["sweep_ms"][6] / 3,
-                   "force_pairs_per_s": vst["sweep_units"][6] / 2 / (vst["sweep_ms"][6] / 1e3),
-                   "kernels": ["k_sweep<PVelDeriv>", "k_sweep<PForceVisc>"]}
+        vst = hs.stats()
+        hs.profile(False)
+        extras["viscous_force"] = {
+            "workload": args.side_workload,
+            "velocity_derivatives_ms": vst["sweep_ms"][5] / 3,
+            "viscous_force_ms": vst["sweep_ms"][6] / 3,
+            "force_pairs_per_s": vst["sweep_units"][6] / 2 / (vst["sweep_ms"][6] / 1e3),
+            "kernels": ["k_sweep<PVelDeriv>", "k_sweep<PForceVisc>"]}
+        hs.close()
+        del spos, sm_, su, sv
+        # ---- the other configurations, briefly
+        others = {}
+        for name in [x for x in args.others.split(",") if x and x != args.workload]:
+            try:
+                others[name] = other_workload(name, dev, params)
+            except Exception as e:  # noqa: BLE001
+                others[name] = {"failed": str(e)}
+        extras["other_workloads"] = others
+        try:
+            extras["parity_small_full_oracle"] = small_parity(dev)
+        except Exception as e:  # noqa: BLE001
+            extras["parity_small_full_oracle"] = {"failed": str(e)}
+
     cpu = None
     parity = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -481,13 +636,18 @@ def main():
             cpu = {"value": r["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"{r['sample']} random particles of {args.workload}, evaluated from "
                              f"scratch in {r['seconds']:.1f} s (h solve of the sample and its "
-                             "force partners, density, force)"}
+                             "force partners, density, force; the neighbour trees of the whole "
+                             "set included)"}
+            try:
+                cpu["whole_small_box"] = oracle_full_rate()
+            except Exception as e:  # noqa: BLE001
+                cpu["whole_small_box"] = {"failed": str(e)}
             # the oracle's values of that sample against this run's results
             try:
                 gi, ref = r["index"], r["ref"]
                 gh = den["h"].double().cpu().numpy()[gi]
                 grho = den["rho"].double().cpu().numpy()[gi]
-                ga = acc.double().cpu().numpy()[gi]
+                ga = out[1].double().cpu().numpy()[gi]
                 arms = float(np.sqrt(np.mean(np.sum(ref["a"] ** 2, axis=1))))
                 parity = {"particles": int(len(gi)),
                           "max_rel_err_h": float(np.max(np.abs(gh / ref["h"] - 1.0))),
@@ -501,25 +661,30 @@ def main():
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {e}"}
     if rank == 0:
+        ratio = (fwd_ms + adj_ms) / fwd_ms
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "particles": n,
-                       "units_per_step": units, "density_interactions": st["density_interactions"],
-                       "force_pairs": st["force_pairs"],
+                       "units_per_step": units, "density_interactions": dens_units,
+                       "force_pairs": force_units,
                        "step": "build+density(h-solve)+ghost+force+adjoint",
-                       "l2": "working set per step > L2 (sorted lists alone ~%d MB)" % (st["sorted_entries"] * 8 // 2**20),
+                       "l2": "working set per step > L2 (sorted lists alone ~%d MB)"
+                             % (st["sorted_entries"] * 8 // 2**20),
                        "kahan": args.kahan, "parallelism": f"replicas x{world}",
-                       "h_iteration": "CUDA graph, device-side while loop"},
-            "fwd_ms": fwd_ms, "adj_ms": adj_ms, "fwd_adj_over_fwd": (fwd_ms + adj_ms) / fwd_ms,
+                       "h_iteration": "CUDA graph, device-side while loop",
+                       "fwd_adj_over_fwd": ratio,
+                       "plain_fp32_fwd_ms": fwd32_ms, "compensated_fwd_ms": fwd_ms},
+            "fwd_ms": fwd_ms, "adj_ms": adj_ms, "fwd_adj_over_fwd": ratio,
             "fwd_value": units / (fwd_ms / 1e3),
+            "plain_fp32_forward": plain32,
             "clocks": clocks,
             "e2e": {"value": job_rate(units, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "profiled_pass": {"ms_per_step": prof["ms"], "gpu_launches": int(prof["launches"]),
-                              "clocks": prof["clocks"],
+            "profiled_pass": {"ms_per_step": prof["ms"], "steps": prof["steps"],
+                              "gpu_launches": int(prof["launches"]), "clocks": prof["clocks"],
                               "note": "roofline and kernels come from this pass (host-loop h "
                                       "iteration, CUDA events around every sweep launch)"},
             "autotune": tuned,
@@ -529,12 +694,11 @@ def main():
                                                             "ndt", "max_depth", "newton_iters",
                                                             "rebuilds")},
             "h_iteration_active": [x for x in prod["stats"]["newton_active"] if x],
-            "ablation_naive_vs_sorted": ablation,
-            "viscous_force": viscous,
             "sampled_parity": parity,
-            "build_stages_ms": {BUILD_STAGES[k]: st["build_ms"][k] / args.steps for k in range(8)},
+            "build_stages_ms": {BUILD_STAGES[k]: st["build_ms"][k] / prof["steps"] for k in range(8)},
             "cpu_baseline": cpu,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -134,7 +134,7 @@ typedef struct sph_stats {
                                 phases 0 and 1, ordered i != j pairs for 2..4 */
   int64_t sweep_candidates[8]; /* (i, j) candidates those launches evaluated */
   int32_t newton_active[32]; /* particles still iterating after each of the first 32 h iterations
-                                of the last solve round (0 afterwards) */
+                                of the last sph_density, rounds after a rebuild included (0 afterwards) */
   int32_t unconverged;       /* particles left unconverged by the last sph_density */
   int32_t sweep_grid;        /* CTAs of the last sweep launch */
   int32_t sweep_threads;     /* threads per CTA of the sweep launches */
@@ -306,9 +306,11 @@ int sph_get_stats(sph_ctx* ctx, sph_stats* out);
  * allocation may block or fail, or applications that must not grow their
  * device footprint after start-up.
  *
- * Density with the smoothing-length solve of Eq. (nneigh) for ONE small
- * periodic box [0, box)^3, by direct summation over all particle pairs (no
- * cell decomposition, no context), allocating nothing.  The per-particle
+ * Density with the smoothing-length solve for ONE small periodic box
+ * [0, box)^3: each h_i is moved by Newton steps inside an FP64 bracket until
+ * the weighted neighbour number (32/3) sum_j w(r_ij/h_i) equals n_ngb, with
+ * every sum taken by direct summation over all particle pairs (no cell
+ * decomposition, no context), allocating nothing.  The per-particle
  * solver scratch (FP64 bracket, flags, sums) lives in a file-scope device
  * array sized for SPH_NOALLOC_MAX_N particles (about 0.6 MB) that every
  * GPU loading this library holds until the process exits.
@@ -318,15 +320,17 @@ int sph_get_stats(sph_ctx* ctx, sph_stats* out);
  *   m        n float32 masses (device)
  *   h_guess  n float32 initial h (device, nullable: the h holding n_ngb
  *            particles at the mean density)
- *   n_ngb    target weighted neighbour number (48 in the paper)
+ *   n_ngb    target weighted neighbour number (> 32/3; 48 is usual)
  *   max_iter Newton/bisection iterations at most
- *   h_out, rho_out  n float32 outputs (device; either may be NULL)
+ *   h_out, rho_out  n float32 outputs (device; either may be NULL); rho_out
+ *            is always the density at the h written to h_out
  *   iters    out (HOST, nullable): iterations used
  * Returns SPH_ERR_CELL_LIMIT if some h would exceed box/2 and
  * SPH_ERR_H_NOT_CONVERGED after max_iter.  Synchronises `stream`.
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array,
+ * Every call looks up the scratch array's device address on the current
+ * device (cudaGetSymbolAddress); the first call on a device also loads the
+ * library's device code there, so make that first call before any stream
+ * capture.  Every call on a device shares the one array,
  * which keeps the last call's contents: calls that overlap on the GPU
  * (different streams or host threads) race and must be serialised by the
  * caller. */
@@ -338,6 +342,14 @@ int sph_density_small_noalloc(int32_t n, const double* pos, double box, const fl
 /* Number of kernel launches this library has issued since it was loaded
  * (all contexts). */
 int64_t sph_launch_count(void);
+
+/* A counter that changes with every call that replaces the context's
+ * forward state (sph_build*, sph_density*, sph_force*); the adjoint calls
+ * always differentiate the state of the latest such calls, so a caller that
+ * holds on to a forward (an autograd graph) compares the counter before
+ * asking for its adjoint.  -1 for NULL.  (Bookkeeping; no counterpart in
+ * the paper.) */
+int64_t sph_state_generation(const sph_ctx* ctx);
 
 /* Synchronise `stream` and return (then clear) the device status word. */
 int sph_sync_status(sph_ctx* ctx, void* stream);

@@ -71,6 +71,7 @@ SIGNATURES = {
     "sph_profile": (C.c_int, [P, C.c_int32]),
     "sph_set_sweep_config": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
     "sph_launch_count": (C.c_int64, []),
+    "sph_state_generation": (C.c_int64, [P]),
     "sph_density_small_noalloc": (C.c_int, [C.c_int32, P, C.c_double, P, P, C.c_float, C.c_int32,
                                             P, P, C.POINTER(C.c_int32), P]),
     "sph_sync_status": (C.c_int, [P, P]),

@@ -12,7 +12,7 @@ namespace {
 constexpr int TPB = 256;
 constexpr float SIGMA = 2.546479089470325f;  // 8/pi
 
-enum : int { HF_ACTIVE = 1, HF_HI_VALID = 2, HF_LIMIT = 4 };
+enum : int { HF_ACTIVE = 1, HF_HI_VALID = 2, HF_LIMIT = 4, HF_LO_VALID = 8 };
 
 __global__ void k_fill_mass(long long n, const int* perm, const float* m, float4* pos4) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -49,82 +49,157 @@ __global__ void k_check_h(long long n, const float* h, const float* hlim, int* s
 // ---- smoothing-length solve (Eq. (nneigh)): Newton steps on
 // ln N(ln h) = ln n_ngb (the paper's Newton iteration with dN/dh computed
 // alongside the sums, taken in log-log form so that it lands on the root in
-// one step when N grows like h^3), safeguarded by an FP64 bracket [lo, hi]:
-// a step that leaves the bracket, or that is not at least twice shorter than
-// the step before it, is replaced by bisection, so the bracket keeps
-// shrinking even where N(h) is steep.
-__global__ void k_hsolve_init(long long n, float* h, const float* hlim, double* lo, double* hi,
-                              float* dxold, int* flag) {
-  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  float hl = hlim[s];
-  float v = h[s];
-  if (!(v > 0.f) || v > hl) v = hl;
-  h[s] = v;
-  lo[s] = 0.0;
-  hi[s] = (double)hl;
-  dxold[s] = 1e30f;
-  flag[s] = HF_ACTIVE;
-}
+// one step when N grows like h^3, with the Halley correction from d2N/dh2),
+// safeguarded by an FP64 bracket [lo, hi].  Where the local step leaves the
+// bracket (N can steepen abruptly: a dense group of neighbours entering the
+// kernel support at once contributes (1 - r/h)^3 terms that the derivatives
+// at the current h do not see), the step is the root of the cubic Hermite
+// interpolant of g = ln(N / n_ngb) over the bracket, built from g and dg/dlnh
+// recorded at both ends; bisection remains the last resort, so the bracket
+// keeps shrinking.
+struct HSolve {
+  float* h;
+  const float* hlim;
+  const float* nngb;
+  const float* dnngb;
+  const float* d2nngb;
+  double* lo;
+  double* hi;
+  float4* gb;      // g and dg/dlnh at the lower end (x, y) and the upper end (z, w)
+  float* dxold;
+  int* flag;
+  float n_ngb, tol;
+  int* nactive;
+  int* nlimit;
+};
 
-__global__ void k_hsolve_update(long long n, float* h, const float* hlim, const float* nngb,
-                                const float* dnngb, const float* d2nngb, double* lo, double* hi,
-                                float* dxold, int* flag, float n_ngb, float tol, int* nactive,
-                                int* nlimit) {
+// mode 0: every particle starts; mode 1 (after a rebuild): only the particles
+// whose root lay beyond their old cell limit restart, with the old limit as
+// their evaluated lower end; the others keep their converged h and sums
+__global__ void k_hsolve_init(long long n, HSolve S, int mode) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  int fl = flag[s];
-  if (!(fl & HF_ACTIVE)) return;
-  const double hd = (double)h[s];
-  const float Nv = nngb[s];
-  const double f = (double)Nv - (double)n_ngb;
-  if (fabs(f) <= (double)tol * (double)n_ngb) {
-    flag[s] = fl & ~HF_ACTIVE;
+  const float hl = S.hlim[s];
+  if (mode == 1) {
+    const int fl = S.flag[s];
+    if (!(fl & HF_LIMIT)) {
+      S.flag[s] = 0;
+      return;
+    }
+    S.hi[s] = (double)hl;
+    S.dxold[s] = 1e30f;
+    S.flag[s] = HF_ACTIVE | HF_LO_VALID;  // lo and gb.xy hold the old limit's values
     return;
   }
-  double L = lo[s], H = hi[s];
-  const double hl = (double)hlim[s];
+  float v = S.h[s];
+  if (!(v > 0.f) || v > hl) v = hl;
+  S.h[s] = v;
+  S.lo[s] = 0.0;
+  S.hi[s] = (double)hl;
+  S.dxold[s] = 1e30f;
+  S.flag[s] = HF_ACTIVE;
+}
+
+// root in (0, 1) of the cubic Hermite interpolant with values p0 < 0 < p1 and
+// slopes m0, m1 (per unit t) at t = 0 and t = 1: Newton steps kept inside a
+// shrinking sub-bracket; -1 if no usable root
+__device__ double hermite_root(double p0, double m0, double p1, double m1) {
+  double a = 0.0, b = 1.0;
+  double t = p0 / (p0 - p1);  // the secant point
+  for (int it = 0; it < 24; ++it) {
+    const double t2 = t * t, t3 = t2 * t;
+    const double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + t, h01 = -2 * t3 + 3 * t2,
+                 h11 = t3 - t2;
+    const double c = h00 * p0 + h10 * m0 + h01 * p1 + h11 * m1;
+    const double dc = (6 * t2 - 6 * t) * p0 + (3 * t2 - 4 * t + 1) * m0 + (-6 * t2 + 6 * t) * p1 +
+                      (3 * t2 - 2 * t) * m1;
+    if (c < 0) a = t; else b = t;
+    if (fabs(c) < 1e-12) return t;
+    double tn = dc > 0 ? t - c / dc : -1.0;
+    if (!(tn > a && tn < b)) tn = 0.5 * (a + b);
+    if (fabs(tn - t) < 1e-14) return tn;
+    t = tn;
+  }
+  return (b - a) < 1e-6 ? 0.5 * (a + b) : -1.0;
+}
+
+__global__ void k_hsolve_update(long long n, HSolve S) {
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int fl = S.flag[s];
+  if (!(fl & HF_ACTIVE)) return;
+  const double hd = (double)S.h[s];
+  const float Nv = S.nngb[s];
+  const double f = (double)Nv - (double)S.n_ngb;
+  if (fabs(f) <= (double)S.tol * (double)S.n_ngb) {
+    S.flag[s] = fl & ~HF_ACTIVE;
+    return;
+  }
+  double L = S.lo[s], H = S.hi[s];
+  float4 gb = S.gb[s];
+  const double hl = (double)S.hlim[s];
+  // g(x) = ln N - ln n_ngb and g'(x) = h N'/N in x = ln h
+  const float slope = (S.dnngb[s] > 0.f && Nv > 0.f) ? (float)(hd * (double)S.dnngb[s] / (double)Nv) : 0.f;
+  const float g = __logf(Nv) - __logf(S.n_ngb);
   if (f < 0) {
     L = hd;
+    gb.x = g;
+    gb.y = slope;
+    fl |= HF_LO_VALID;
     if (hd >= hl) {  // the root lies beyond what this decomposition covers
-      flag[s] = HF_LIMIT;
-      atomicAdd(nlimit, 1);
+      S.lo[s] = L;
+      S.gb[s] = gb;
+      S.flag[s] = HF_LIMIT | HF_LO_VALID;
+      atomicAdd(S.nlimit, 1);
       return;
     }
   } else {
     H = hd;
+    gb.z = g;
+    gb.w = slope;
     fl |= HF_HI_VALID;
   }
-  // Halley step in x = ln h on g(x) = ln N - ln n_ngb, with g'(x) = h N'/N
-  // and g''(x) = g' + h^2 N''/N - g'^2 (cubic convergence near the root;
-  // the Newton step g/g' where the correction is not well conditioned)
-  const float slope = (dnngb[s] > 0.f && Nv > 0.f) ? (float)(hd * (double)dnngb[s] / (double)Nv) : 0.f;
-  const float g = __logf(Nv) - __logf(n_ngb);
-  float dx = slope > 1e-3f ? g / slope : 0.f;  // ln(h / h_new)
+  // Halley step ln(h / h_new) from the current point, with
+  // g''(x) = g' + h^2 N''/N - g'^2 (the Newton step g/g' where the
+  // correction is not well conditioned)
+  float dx = slope > 1e-3f ? g / slope : 0.f;
   if (slope > 1e-3f) {
     const float hf0 = (float)hd;
-    const float curv = slope + hf0 * hf0 * d2nngb[s] / Nv - slope * slope;
+    const float curv = slope + hf0 * hf0 * S.d2nngb[s] / Nv - slope * slope;
     const float den = 2.f * slope * slope - g * curv;
     if (den > slope * slope) dx = 2.f * g * slope / den;
   }
+  const float dxprev = S.dxold[s];
   double hn;
   float step;
   if (fl & HF_HI_VALID) {
+    if (H - L <= 2.4e-7 * hd) {  // bracket below FP32 resolution
+      S.lo[s] = L;
+      S.hi[s] = H;
+      S.gb[s] = gb;
+      S.flag[s] = fl & ~HF_ACTIVE;
+      return;
+    }
     const double prop = slope > 1e-3f ? hd * (double)__expf(-dx) : -1.0;
     const bool out = !(prop > L && prop < H);
-    const bool slow = fabsf(2.f * g) > fabsf(dxold[s] * slope);
-    if (out || slow || slope <= 1e-3f) {
-      hn = L > 0 ? sqrt(L * H) : 0.5 * (L + H);  // bisection (geometric once L > 0)
+    const bool slow = fabsf(2.f * g) > fabsf(dxprev * slope);
+    hn = -1.0;
+    if (!(out || slow || slope <= 1e-3f)) {
+      hn = prop;
+    } else if ((fl & HF_LO_VALID) && L > 0 && gb.y > 0.f && gb.w > 0.f) {
+      // cubic Hermite interpolation of g over [ln L, ln H]
+      const double w = log(H / L);
+      const double t = hermite_root((double)gb.x, (double)gb.y * w, (double)gb.z, (double)gb.w * w);
+      if (t > 0.0 && t < 1.0) {
+        const double q = L * exp(t * w);
+        if (q > L && q < H && fabs(log(q / hd)) <= 0.5f * dxprev) hn = q;
+      }
+    }
+    if (hn > 0) {
       step = (float)fabs(log(hn / hd));
     } else {
-      hn = prop;
-      step = fabsf(dx);
-    }
-    if (H - L <= 2.4e-7 * hd) {  // bracket below FP32 resolution
-      lo[s] = L;
-      hi[s] = H;
-      flag[s] = fl & ~HF_ACTIVE;
-      return;
+      hn = L > 0 ? sqrt(L * H) : 0.5 * (L + H);  // bisection (geometric once L > 0)
+      step = (float)fabs(log(hn / hd));
     }
   } else {
     // no upper end yet: Newton upwards, doubling when it has no slope, capped
@@ -134,17 +209,18 @@ __global__ void k_hsolve_update(long long n, float* h, const float* hlim, const 
     hn = fmin(hn, hl);
     step = (float)fabs(log(hn / hd));
   }
-  lo[s] = L;
-  hi[s] = H;
-  dxold[s] = step;
+  S.lo[s] = L;
+  S.hi[s] = H;
+  S.gb[s] = gb;
+  S.dxold[s] = step;
   const float hf = (float)hn;
-  if (hf == h[s] || step < 1e-7f) {  // no FP32-representable progress left
-    flag[s] = fl & ~HF_ACTIVE;
+  if (hf == S.h[s] || step < 1e-7f) {  // no FP32-representable progress left
+    S.flag[s] = fl & ~HF_ACTIVE;
     return;
   }
-  h[s] = hf;
-  flag[s] = fl;
-  atomicAdd(nactive, 1);
+  S.h[s] = hf;
+  S.flag[s] = fl;
+  atomicAdd(S.nactive, 1);
 }
 
 // body end of the device-side h iteration: record this iteration's active
@@ -169,11 +245,21 @@ __global__ void k_block_active(int nblock, const int* b_first, const int* b_coun
   if (lane == 0) act[warp] = any;
 }
 
+// build guess of the next decomposition: the current h, and for particles
+// whose root lies beyond their cell limit the larger of twice the limit and
+// the h at which N would reach n_ngb if it grew like h^3 from its value at
+// the limit (with a 25 % margin)
 __global__ void k_rebuild_guess(long long n, const float* h, const float* hlim, const int* flag,
-                                float* hg) {
+                                const float* nngb, float n_ngb, float* hg) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  hg[s] = (flag[s] & HF_LIMIT) ? 2.0f * hlim[s] : h[s];
+  if (flag[s] & HF_LIMIT) {
+    const float hl = hlim[s], N = nngb[s];
+    const float ext = N > 0.f ? 1.25f * cbrtf(n_ngb / N) : 2.f;
+    hg[s] = hl * fmaxf(2.f, ext);
+  } else {
+    hg[s] = h[s];
+  }
 }
 
 // ---- ghost step (text after Eq. (dudt)) and force-side per-particle data
@@ -238,6 +324,7 @@ __global__ void k_sum_i32(long long n, const int* v, unsigned long long* out) {
 static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 static int status_from_word(int w) {
+  if (w & ST_BAD_INPUT) return SPH_ERR_INVALID_ARG;
   if (w & ST_CAPACITY) return SPH_ERR_CAPACITY;
   if (w & ST_TIMEOUT) return SPH_ERR_TIMEOUT;
   if (w & ST_CELL_LIMIT) return SPH_ERR_CELL_LIMIT;
@@ -266,9 +353,29 @@ static int ensure_state(sph_ctx* c) {
   SPH_TRY(dbuf_ensure(c->h_hi, 8 * n));
   SPH_TRY(dbuf_ensure(c->h_flag, 4 * n));
   SPH_TRY(dbuf_ensure(c->h_dx, 4 * n));
+  SPH_TRY(dbuf_ensure(c->h_gb, 16 * n));
   SPH_TRY(dbuf_ensure(c->blk_active, 4 * (size_t)(c->nblock + 1)));
   SPH_TRY(dbuf_ensure(c->tmp_a, 64));
   return SPH_OK;
+}
+
+static HSolve hsolve_args(sph_ctx* c, int* nactive, int* nlimit) {
+  HSolve S;
+  S.h = c->h.as<float>();
+  S.hlim = c->hlim.as<float>();
+  S.nngb = c->nngb.as<float>();
+  S.dnngb = c->dnngb.as<float>();
+  S.d2nngb = c->d2nngb.as<float>();
+  S.lo = c->h_lo.as<double>();
+  S.hi = c->h_hi.as<double>();
+  S.gb = c->h_gb.as<float4>();
+  S.dxold = c->h_dx.as<float>();
+  S.flag = c->h_flag.as<int>();
+  S.n_ngb = c->prm.n_ngb;
+  S.tol = c->prm.h_tol;
+  S.nactive = nactive;
+  S.nlimit = nlimit;
+  return S;
 }
 
 static int count_total(sph_ctx* c, unsigned long long* out, cudaStream_t s) {
@@ -293,7 +400,7 @@ static void graph_release(sph_ctx* c) {
 // on the device until no particle is iterating or max_newton is reached;
 // the host reads the counters once at the end.  The graph bakes in the
 // decomposition's buffers, so it is captured again after every build.
-static int solve_round_graph(sph_ctx* c, cudaStream_t s, int* host, int* iters) {
+static int solve_round_graph(sph_ctx* c, cudaStream_t s, int* host, int* iters, int hist0) {
   const long long n = c->n;
   int* ctl = c->solve_ctl.as<int>();  // [0] active [1] at limit [2] iteration [3..34] history
   if (!c->g_exec || c->g_gen != c->build_gen) {
@@ -320,10 +427,7 @@ static int solve_round_graph(sph_ctx* c, cudaStream_t s, int* host, int* iters) 
         c->blk_active.as<int>()); note_launch(); }
     if (r == SPH_OK) r = run_sweep(c, PH_DENSITY, 1, 0, cs);
     if (r == SPH_OK && cudaMemsetAsync(ctl, 0, sizeof(int), cs) != cudaSuccess) r = SPH_ERR_CUDA;
-    { k_hsolve_update<<<div_up(n, TPB), TPB, 0, cs>>>(
-        n, c->h.as<float>(), c->hlim.as<float>(), c->nngb.as<float>(), c->dnngb.as<float>(),
-        c->d2nngb.as<float>(), c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_dx.as<float>(),
-        c->h_flag.as<int>(), c->prm.n_ngb, c->prm.h_tol, ctl, ctl + 1); note_launch(); }
+    { k_hsolve_update<<<div_up(n, TPB), TPB, 0, cs>>>(n, hsolve_args(c, ctl, ctl + 1)); note_launch(); }
     { k_loop_ctl<<<1, 1, 0, cs>>>(ctl, ctl + 2, ctl + 3, c->prm.max_newton, hnd); note_launch(); }
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &captured);
@@ -343,7 +447,7 @@ static int solve_round_graph(sph_ctx* c, cudaStream_t s, int* host, int* iters) 
   host[1] = h_ctl[1];
   *iters = h_ctl[2];
   note_launch_n(c->g_body_kernels * h_ctl[2]);  // body kernels the graph ran
-  for (int k = 0; k < 32; ++k) c->stats.newton_active[k] = h_ctl[3 + k];
+  for (int k = 0; k < 32 && hist0 + k < 32; ++k) c->stats.newton_active[hist0 + k] = h_ctl[3 + k];
   return SPH_OK;
 }
 
@@ -420,7 +524,7 @@ void sph_destroy(sph_ctx* c) {
                  &c->b_dtoff, &c->b_order, &c->b_cost, &c->dt_cj, &c->dt_code, &c->dt_shift,
                  &c->adj_off, &c->adj_list, &c->s_key, &c->s_idx, &c->rho, &c->drho, &c->nngb,
                  &c->dnngb, &c->d2nngb, &c->d2rho, &c->omega, &c->Avec, &c->fdat, &c->vel4, &c->u_s, &c->acc4,
-                 &c->cnt_i, &c->h_lo, &c->h_hi, &c->h_dx, &c->h_flag, &c->blk_active, &c->adj4, &c->adj4b, &c->g_A,
+                 &c->cnt_i, &c->h_lo, &c->h_hi, &c->h_dx, &c->h_gb, &c->h_flag, &c->blk_active, &c->adj4, &c->adj4b, &c->g_A,
                  &c->g_rho_s, &c->g_drho_s, &c->g_h_s, &c->g_u_s, &c->g_x4,
                  &c->prof_units, &c->solve_ctl, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
                  &c->tmp_b, &c->tmp_c, &c->p_et, &c->nleaf_dev, &c->n_listed, &c->n_ex, &c->n_lo,
@@ -448,6 +552,7 @@ int sph_build_batch(sph_ctx* c, int32_t nbox, const int64_t* offsets, const doub
   long long n = offsets[nbox];
   if (n <= 0 || n >= (1ll << 31) / 16) return SPH_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
+  ++c->state_gen;
   c->built = c->have_density = c->have_force = false;
   c->fl_valid = false;
   c->have_d2 = 0;
@@ -489,6 +594,7 @@ int sph_density_fixed_h(sph_ctx* c, const float* m, const float* h, float* rho, 
                         float* nngb, float* dnngb_dh, int32_t* count, void* stream) {
   if (!c || !m || !h || !rho) return SPH_ERR_INVALID_ARG;
   if (!c->built) return SPH_ERR_NOT_BUILT;
+  ++c->state_gen;
   cudaStream_t s = as_stream(stream);
   const long long n = c->n;
   SPH_TRY(prep_mass(c, m, s));
@@ -524,26 +630,27 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
                 int32_t* iters, void* stream) {
   if (!c || !m) return SPH_ERR_INVALID_ARG;
   if (!c->built) return SPH_ERR_NOT_BUILT;
+  ++c->state_gen;
   cudaStream_t s = as_stream(stream);
   const long long n = c->n;
   SPH_TRY(prep_mass(c, m, s));
   int total_iters = 0, rebuilds = 0;
   int* nact = c->tmp_a.as<int>();
   int* nlim = nact + 1;
+  for (int k = 0; k < 32; ++k) c->stats.newton_active[k] = 0;
   for (;;) {
-    { k_hsolve_init<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), c->hlim.as<float>(),
-                                                 c->h_lo.as<double>(), c->h_hi.as<double>(),
-                                                 c->h_dx.as<float>(), c->h_flag.as<int>()); note_launch(); }
+    // the first round starts every particle; a round after a rebuild only
+    // the particles whose root lay beyond their old cell limit
+    { k_hsolve_init<<<div_up(n, TPB), TPB, 0, s>>>(n, hsolve_args(c, nact, nlim), rebuilds > 0 ? 1 : 0); note_launch(); }
     SPH_CUDA(cudaGetLastError());
     int host[2] = {1, 0};
     int it = 0;
-    for (int k = 0; k < 32; ++k) c->stats.newton_active[k] = 0;
     SPH_CUDA(cudaMemsetAsync(c->blk_active.p, 0, 4 * (size_t)c->nblock, s));
     // nlim accumulates over the whole solve: a particle flagged at its cell
     // limit in any iteration leaves the active set and must trigger the rebuild
     SPH_CUDA(cudaMemsetAsync(nlim, 0, sizeof(int), s));
     if (c->prm.use_graph && !c->profile) {
-      SPH_TRY(solve_round_graph(c, s, host, &it));
+      SPH_TRY(solve_round_graph(c, s, host, &it, total_iters));
     } else {
     for (; it < c->prm.max_newton; ++it) {
       { k_block_active<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, s>>>(
@@ -552,14 +659,11 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
       SPH_CUDA(cudaGetLastError());
       SPH_TRY(run_sweep(c, PH_DENSITY, 1, 0, s));
       SPH_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), s));
-      { k_hsolve_update<<<div_up(n, TPB), TPB, 0, s>>>(
-          n, c->h.as<float>(), c->hlim.as<float>(), c->nngb.as<float>(), c->dnngb.as<float>(),
-          c->d2nngb.as<float>(), c->h_lo.as<double>(), c->h_hi.as<double>(), c->h_dx.as<float>(),
-          c->h_flag.as<int>(), c->prm.n_ngb, c->prm.h_tol, nact, nlim); note_launch(); }
+      { k_hsolve_update<<<div_up(n, TPB), TPB, 0, s>>>(n, hsolve_args(c, nact, nlim)); note_launch(); }
       SPH_CUDA(cudaGetLastError());
       SPH_CUDA(cudaMemcpyAsync(host, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       SPH_CUDA(cudaStreamSynchronize(s));
-      if (it < 32) c->stats.newton_active[it] = host[0];
+      if (total_iters + it < 32) c->stats.newton_active[total_iters + it] = host[0];
       if (host[0] == 0) {
         ++it;
         break;
@@ -579,7 +683,8 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
     }
     ++rebuilds;
     { k_rebuild_guess<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), c->hlim.as<float>(),
-                                                   c->h_flag.as<int>(), c->hguess.as<float>()); note_launch(); }
+                                                   c->h_flag.as<int>(), c->nngb.as<float>(),
+                                                   c->prm.n_ngb, c->hguess.as<float>()); note_launch(); }
     SPH_CUDA(cudaGetLastError());
     {
       int r = build_from_guess(c, s);
@@ -621,6 +726,7 @@ int sph_force(sph_ctx* c, const float* u, const float* vel, float* acc, float* d
               int32_t* count, void* stream) {
   if (!c || !u || !acc) return SPH_ERR_INVALID_ARG;
   if (!c->have_density) return SPH_ERR_NOT_BUILT;
+  ++c->state_gen;
   cudaStream_t s = as_stream(stream);
   const long long n = c->n;
   const int* perm = c->perm.as<int>();
@@ -650,6 +756,7 @@ int sph_force_viscous(sph_ctx* c, const float* u, const float* vel, float alpha,
   if (!c || !u || !vel || !acc || !dt || !(alpha >= 0.f) || !(c_cfl > 0.f))
     return SPH_ERR_INVALID_ARG;
   if (!c->have_density) return SPH_ERR_NOT_BUILT;
+  ++c->state_gen;
   cudaStream_t s = as_stream(stream);
   const long long n = c->n;
   const int* perm = c->perm.as<int>();
@@ -769,6 +876,8 @@ int sph_sync_status(sph_ctx* c, void* stream) {
 }
 
 int64_t sph_launch_count(void) { return (int64_t)launch_count(); }
+
+int64_t sph_state_generation(const sph_ctx* c) { return c ? (int64_t)c->state_gen : -1; }
 
 const char* sph_status_string(int st) {
   switch (st) {

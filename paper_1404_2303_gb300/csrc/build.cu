@@ -61,7 +61,7 @@ __device__ __forceinline__ float warp_max(float v) {
 
 // ---------------------------------------------------------------- keys
 __global__ void k_keys(const double* pos, long long n, const long long* off, const double* Ls,
-                       int nbox, int K, unsigned long long* keys, int* perm) {
+                       int nbox, int K, unsigned long long* keys, int* perm, int* status) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= n) return;
   int b = box_of(off, nbox, p);
@@ -69,7 +69,9 @@ __global__ void k_keys(const double* pos, long long n, const long long* off, con
   double scale = (double)(1u << K) / L;
   unsigned q[3];
   for (int k = 0; k < 3; ++k) {
-    double x = wrap_pos(pos[3 * p + k], L);
+    const double x0 = pos[3 * p + k];
+    if (!isfinite(x0)) atomicOr(status, ST_BAD_INPUT);  // reported by the build; key clamped below
+    double x = isfinite(x0) ? wrap_pos(x0, L) : 0.0;
     long long v = (long long)floor(x * scale);
     v = v < 0 ? 0 : (v > (1ll << K) - 1 ? (1ll << K) - 1 : v);
     q[k] = (unsigned)v;
@@ -80,14 +82,24 @@ __global__ void k_keys(const double* pos, long long n, const long long* off, con
 
 __global__ void k_gather_pos(const double* pos, const int* perm, long long n, const long long* off,
                              const double* Ls, int nbox, const float* hg_in, double* xs,
-                             float* hg_out) {
+                             float* hg_out, int* status) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
   int p = perm[s];
   int b = box_of(off, nbox, p);
   double L = Ls[b];
-  for (int k = 0; k < 3; ++k) xs[3 * s + k] = wrap_pos(pos[3 * (long long)p + k], L);
-  if (hg_in) hg_out[s] = hg_in[p];
+  for (int k = 0; k < 3; ++k) {
+    const double x0 = pos[3 * (long long)p + k];
+    xs[3 * s + k] = isfinite(x0) ? wrap_pos(x0, L) : 0.0;
+  }
+  if (hg_in) {
+    float g = hg_in[p];
+    if (!(g > 0.f) || !isfinite(g)) {  // a guess must be a positive finite length
+      atomicOr(status, ST_BAD_INPUT);
+      g = (float)(0.25 * L);
+    }
+    hg_out[s] = g;
+  }
 }
 
 // ---------------------------------------------------------------- octree
@@ -1627,7 +1639,8 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
   SPH_TRY(dbuf_ensure(c->p_et, 4 * (size_t)n));
   { k_keys<<<div_up(n, TPB), TPB, 0, s>>>(pos, n, c->d_box_off.as<long long>(),
                                         c->d_box_L.as<double>(), c->nbox, K,
-                                        c->keys.as<unsigned long long>(), c->perm.as<int>()); note_launch(); }
+                                        c->keys.as<unsigned long long>(), c->perm.as<int>(),
+                                        c->status.as<int>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   SPH_TRY(radix_sort_u64(c->keys.as<unsigned long long>(), c->perm.as<int>(),
                          c->keys_alt.as<unsigned long long>(), c->perm_alt.as<int>(), (int)n,
@@ -1635,7 +1648,8 @@ int build_decomposition(sph_ctx* c, const double* pos, const float* h_guess, cud
   { k_gather_pos<<<div_up(n, TPB), TPB, 0, s>>>(pos, c->perm.as<int>(), n,
                                               c->d_box_off.as<long long>(),
                                               c->d_box_L.as<double>(), c->nbox, h_guess,
-                                              c->xs.as<double>(), c->hguess.as<float>()); note_launch(); }
+                                              c->xs.as<double>(), c->hguess.as<float>(),
+                                              c->status.as<int>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   SPH_TRY(build_mark(c, s, 0));
   if (!h_guess) {

@@ -39,6 +39,7 @@ enum : int {
   ST_CAPACITY = 4,
   ST_BAD_INDEX = 8,
   ST_TIMEOUT = 16,
+  ST_BAD_INPUT = 32,  // a non-finite position or a non-positive h guess
 };
 
 // ---------------------------------------------------------------------------
@@ -79,6 +80,7 @@ struct sph_ctx {
   std::vector<int> box_t;          // log2 top cells per axis
   std::vector<int> top_base;       // first top-cell node per box (nbox+1)
   bool built = false;
+  long long state_gen = 0;  // bumped by every call that replaces the forward state
   bool have_density = false;
   bool have_force = false;
   int have_d2 = 0;
@@ -149,6 +151,7 @@ struct sph_ctx {
   // h solver
   DBuf h_lo, h_hi;   // double bracket
   DBuf h_dx;         // float previous |step| in ln h
+  DBuf h_gb;         // float4 g = ln(N/n_ngb) and dg/dln h at the bracket ends
   DBuf h_flag;       // int: bit0 active, bit1 hi evaluated, bit2 cell limit
   DBuf blk_active;   // int per block
   // adjoint state

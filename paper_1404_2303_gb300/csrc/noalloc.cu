@@ -18,7 +18,6 @@
 // host threads) race; it keeps the last call's contents, and each call
 // clears what must start at zero.
 #include <cmath>
-#include <mutex>
 
 #include "internal.cuh"
 
@@ -26,7 +25,6 @@ namespace {
 
 constexpr int NA_MAX = SPH_NOALLOC_MAX_N;
 constexpr int NA_TPB = 128;
-constexpr int NA_MAX_DEV = 64;
 constexpr float NA_SIGMA = 2.546479089470325f;  // 8/pi
 
 struct NoallocScratch {
@@ -43,10 +41,8 @@ struct NoallocScratch {
 
 static __device__ __align__(256) NoallocScratch g_na_scratch;
 
-// Host-side stand-in of g_na_scratch is not a device address: the address is
-// looked up per device (with that device current) and cached here.
-NoallocScratch* g_na_addr[NA_MAX_DEV] = {nullptr};
-std::mutex g_na_mutex;
+// In host code g_na_scratch names a host-side stand-in, not a device
+// address: na_scratch() looks the device address up for the current device.
 
 enum : int { NA_ACTIVE = 1, NA_HI_VALID = 2 };
 
@@ -154,23 +150,19 @@ __global__ void k_na_out(int n, const NoallocScratch* S, float* h_out, float* rh
   if (rho_out) rho_out[i] = S->rho[i];
 }
 
-// once per device, with that device current
+// The device address of the scratch array on the current device.  It is
+// looked up on every call (a cheap host-side lookup once the module is
+// loaded; the first call on a device loads it), so no address is cached
+// across a device reset.
 int na_scratch(NoallocScratch** out) {
-  int dev = 0;
-  SPH_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= NA_MAX_DEV) return SPH_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
-    if (e != cudaSuccess || !p) {
-      fprintf(stderr, "sphgb: cudaGetSymbolAddress of the no-alloc scratch failed: %s\n",
-              cudaGetErrorString(e));
-      return SPH_ERR_CUDA;
-    }
-    g_na_addr[dev] = reinterpret_cast<NoallocScratch*>(p);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+  if (e != cudaSuccess || !p) {
+    fprintf(stderr, "sphgb: cudaGetSymbolAddress of the no-alloc scratch failed: %s\n",
+            cudaGetErrorString(e));
+    return SPH_ERR_CUDA;
   }
-  *out = g_na_addr[dev];
+  *out = reinterpret_cast<NoallocScratch*>(p);
   return SPH_OK;
 }
 
@@ -211,6 +203,13 @@ extern "C" int sph_density_small_noalloc(int32_t n, const double* pos, double bo
       ++it;
       break;
     }
+  }
+  if (host_active) {
+    // out of iterations: the last update moved h of the particles still
+    // iterating, so evaluate rho once more at that h (the outputs then
+    // belong together even though the call reports H_NOT_CONVERGED)
+    { k_na_density<<<grid, NA_TPB, 0, s>>>(n, pos, box, m, S); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
   }
   int host_limit = 0;
   SPH_CUDA(cudaMemcpyAsync(&host_limit, &S->nlimit, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -737,33 +737,49 @@ __device__ __forceinline__ void fold(float* acc, float* cmp, float* part, int ka
   }
 }
 
-// One compute pass over the buffered j-particles.  Without lists every lane
-// evaluates every buffered j (branch-free: the spline's clamps zero the
-// pairs beyond the support), so a warp pays the full interaction for each
-// candidate.  With lists each lane first applies the exact FP32 predicate
-// of its phase to every candidate and records the accepted slots in its own
-// column of a byte list (lane-private, so no synchronisation between the
-// two loops), then evaluates only those: the warp runs as long as its
-// longest list instead of the whole buffer.
+// One compute pass over the buffered j-particles.  A lane evaluates the
+// candidates t = sub, sub + G, sub + 2G, ... for the particle it serves: G = 1
+// (one particle per lane, every candidate) unless the chunk holds few
+// particles, when G lanes share one particle (see k_sweep).  Without lists
+// the evaluation is branch-free (the spline's clamps zero the pairs beyond
+// the support), so a lane pays the full interaction for each candidate.
+// With lists each lane first applies the exact FP32 predicate of its phase
+// to its candidates and records the accepted slots in its own column of a
+// byte list (lane-private, so no synchronisation between the two loops),
+// then evaluates only those: the warp runs as long as its longest list
+// instead of the whole buffer.
 // A phase that records pair lists (WRITES) appends the tag of every
-// accepted pair to the lane's list column wl (entry k at wl[32 k]) while
-// wtot < wcap; wtot keeps counting past the capacity to flag the overflow.
+// accepted pair to its particle's list column wl (entry k at wl[32 k]):
+// the G lanes of a particle write at their exclusive prefix within the
+// group after the group's running total wtot, which keeps counting past the
+// capacity wcap to flag the overflow.
 template <class P, bool COUNT, bool LIST>
 __device__ __forceinline__ void compute_pass(const typename P::I& I, bool vi, const float4* buf,
                                              unsigned char* lst, int staged, int cap, float* part,
-                                             int& cnt, unsigned* wl, int& wtot, int wcap) {
+                                             int& cnt, unsigned* wl, int& wtot, int wcap, int sub,
+                                             int G) {
   __syncwarp();
   if (LIST) {
     const int lane = threadIdx.x & 31;
     int nl = 0;
     if (vi) {
 #pragma unroll 4
-      for (int t = 0; t < staged; ++t) {
+      for (int t = sub; t < staged; t += G) {
         if (P::test(I, buf, t, cap)) {
           lst[nl * 32 + lane] = (unsigned char)t;
           ++nl;
         }
       }
+    }
+    int pre = 0, gtot = nl;
+    if (P::WRITES && G > 1) {  // exclusive prefix of the accepted counts within the group
+      int x = nl;
+      for (int o = 1; o < G; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if ((lane & (G - 1)) >= o) x += y;
+      }
+      pre = x - nl;
+      gtot = __shfl_sync(FULL, x, (lane | (G - 1)));
     }
     const int nmax = __reduce_max_sync(FULL, nl);
     for (int k = 0; k < nmax; ++k) {
@@ -771,14 +787,15 @@ __device__ __forceinline__ void compute_pass(const typename P::I& I, bool vi, co
         const int t = lst[k * 32 + lane];
         P::template interact<COUNT>(I, buf, t, part, cnt, cap);
         if (P::WRITES && wl) {
-          if (wtot < wcap) wl[(size_t)wtot * 32] = __float_as_uint(buf[2 * cap + t].w);
-          ++wtot;
+          const int e = wtot + pre + k;
+          if (e < wcap) wl[(size_t)e * 32] = __float_as_uint(buf[2 * cap + t].w);
         }
       }
     }
+    if (P::WRITES) wtot += gtot;
   } else {
 #pragma unroll 2
-    for (int t = 0; t < staged; ++t) P::template interact<COUNT>(I, buf, t, part, cnt, cap);
+    for (int t = sub; t < staged; t += G) P::template interact<COUNT>(I, buf, t, part, cnt, cap);
   }
   __syncwarp();
 }
@@ -796,10 +813,10 @@ __device__ __forceinline__ void compute_pass(const typename P::I& I, bool vi, co
   } while (0)
 
 // factor-2 band of a particle's h above the block's smallest h (0..15);
-// 31 for particles that need no sweep (converged during the h iteration)
+// 31 for particles that need no sweep (converged during the h iteration, or
+// with a recorded pair list in a masked sweep)
 __device__ __forceinline__ int h_class(const SweepArgs& a, int p, float hmin) {
-  if (!a.pflag) return 0;  // full sweeps keep plain Morton chunks
-  if (!(a.pflag[p] & 1)) return 31;
+  if (a.pflag && !(a.pflag[p] & 1)) return 31;
   const float r = a.h[p] / hmin;
   const int c = r < 2.f ? 0 : (int)__log2f(r);
   return c > 15 ? 15 : c;
@@ -832,11 +849,12 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     if (a.blk_active && a.blk_active[b] == 0) continue;
     const int bf = a.b_first[b], bn = a.b_count[b];
     const long long e0 = a.b_dtoff[b], e1 = a.b_dtoff[b + 1];
-    // During the h iteration only particles still iterating are swept, and
-    // they are grouped by h class (factor-2 bands above the block's smallest
-    // h, Morton order inside a band): chunks share one window per task, set
-    // by their largest h, so a few large-h iterates must not widen the
-    // windows of many small-h ones.  Full sweeps use plain Morton chunks.
+    // The block's particles are swept grouped by h class (factor-2 bands
+    // above the block's smallest h, Morton order inside a band): chunks share
+    // one window per task, set by their largest h, so a few large-h particles
+    // must not widen the windows of many small-h ones (a leaf at the edge of
+    // a dense clump can hold h values three decades apart).  During the h
+    // iteration only particles still iterating are swept.
     float hmin = FLT_MAX;
     for (int k = lane; k < bn; k += 32) hmin = fminf(hmin, a.h[bf + k]);
     hmin = warp_min(hmin);
@@ -857,23 +875,31 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       __syncwarp();
     for (int c0 = 0; c0 < ncls; c0 += 32) {
       const int nc = min(32, ncls - c0);
-      const bool vi = lane < nc;
-      const int pi = bf + ord[c0 + (vi ? lane : 0)];
-      typename P::I I;
-      if (vi) P::load_i(a, pi, I); else P::null_i(I);
-      // chunk geometry: positions, bounding box, largest h
+      // chunk geometry (positions, bounding box, largest h) with lane k
+      // holding chunk particle k
       {
-        float4 me = make_float4(I.x, I.y, I.z, vi ? I.h : 0.f);
-        float4 l0 = make_float4(__shfl_sync(FULL, me.x, 0), __shfl_sync(FULL, me.y, 0),
-                                __shfl_sync(FULL, me.z, 0), 0.f);
-        if (!vi) me = l0;
+        const int po = bf + ord[c0 + (lane < nc ? lane : 0)];
+        const float4 q = a.pos4[po];
+        float4 me = make_float4(q.x, q.y, q.z, lane < nc ? a.h[po] : 0.f);
         cpos[lane] = me;
       }
       const float bx0 = warp_min(cpos[lane].x), bx1 = warp_max(cpos[lane].x);
       const float by0 = warp_min(cpos[lane].y), by1 = warp_max(cpos[lane].y);
       const float bz0 = warp_min(cpos[lane].z), bz1 = warp_max(cpos[lane].z);
-      const float hmx = warp_max(vi ? I.h : 0.f);
+      const float hmx = warp_max(cpos[lane].w);
       __syncwarp();
+      // A chunk of few particles (the last of a block, or a sparse h band:
+      // the large-h particles next to a clump, each with 10^4 - 10^5
+      // candidates) would leave most lanes idle; there G = 32 / nc lanes
+      // (rounded to a power of two) serve each particle, lane l taking chunk
+      // particle l / G and every G-th candidate from l % G, and the G partial
+      // sums are added at the end.
+      const int G = nc > 16 ? 1 : nc > 8 ? 2 : nc > 4 ? 4 : nc > 2 ? 8 : nc > 1 ? 16 : 32;
+      const int slot = lane / G, sub = lane & (G - 1);
+      const bool vi = slot < nc;
+      const int pi = bf + ord[c0 + (vi ? slot : 0)];
+      typename P::I I;
+      if (vi) P::load_i(a, pi, I); else P::null_i(I);
       float acc[P::NACC], cmp[P::NACC], part[P::NACC];
 #pragma unroll
       for (int k = 0; k < P::NACC; ++k) acc[k] = cmp[k] = part[k] = 0.f;
@@ -993,8 +1019,9 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           const unsigned mt = __ballot_sync(FULL, take);
           const int nt = __popc(mt);
           if (staged + nt > cap) {
-            compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot, a.fl_K);
-            if (COUNT && vi) ncand += staged;
+            compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot, a.fl_K,
+                                         sub, G);
+            if (COUNT && vi && sub < staged) ncand += (staged - sub + G - 1) / G;
             fold<P>(acc, cmp, part, a.kahan);
             staged = 0;
           }
@@ -1004,15 +1031,27 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           staged += nt;
         }
       }
-      compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot, a.fl_K);
-      if (COUNT && vi) ncand += staged;
+      compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot, a.fl_K, sub,
+                                   G);
+      if (COUNT && vi && sub < staged) ncand += (staged - sub + G - 1) / G;
       fold<P>(acc, cmp, part, a.kahan);
-      if (vi) {
-        float v[P::NACC];
+      float v[P::NACC];
 #pragma unroll
-        for (int k = 0; k < P::NACC; ++k) v[k] = acc[k] + cmp[k];
+      for (int k = 0; k < P::NACC; ++k) v[k] = acc[k] + cmp[k];
+      int cg = cnt;
+      if (G > 1) {  // the G partial sums of a particle, in a fixed order
+        for (int o = G >> 1; o > 0; o >>= 1) {
+#pragma unroll
+          for (int k = 0; k < P::NACC; ++k) {
+            const float y = __shfl_xor_sync(FULL, v[k], o);
+            v[k] = k >= P::NACC - P::NMAX ? fmaxf(v[k], y) : v[k] + y;
+          }
+          cg += __shfl_xor_sync(FULL, cg, o);
+        }
+      }
+      if (vi && sub == 0) {
         P::finalize(a, pi, v);
-        if (COUNT && a.ocnt) a.ocnt[pi] = cnt;
+        if (COUNT && a.ocnt) a.ocnt[pi] = cg;
         if (wl) {
           const bool over = wtot > a.fl_K;
           a.fl_cnt[pi] = over ? -1 : wtot;

@@ -216,5 +216,10 @@ class SPH:
     def launch_count(self) -> int:
         return int(self.lib.sph_launch_count())
 
+    def generation(self) -> int:
+        """Counter of the forward state; changes with every build, density
+        and force call on this context."""
+        return int(self.lib.sph_state_generation(self.h))
+
     def sync_status(self):
         check(self.lib.sph_sync_status(self.h, _stream()), "sph_sync_status")

@@ -3,8 +3,7 @@ launch per phase, and for the hand-written adjoints (gradients with
 respect to positions, masses and internal energies, h implicit) against
 the FP64 oracle gradient (itself pinned by central differences in the CPU
 suite).  Gradient tolerance: ||g_gpu - g_ref||_2 / ||g_ref||_2 <= 1e-3 per
-quantity, and every element within 1e-3 * rms(g_ref) + 1e-3 |g_ref|... at
-the 99.9th percentile."""
+quantity, and every element within 1e-3 (rms(g_ref) + |g_ref|)."""
 import numpy as np
 import pytest
 import torch
@@ -74,7 +73,7 @@ def _grad_check(d, v=None, g_du=False):
         gg = got.cpu().numpy().astype(np.float64).reshape(want.shape)
         rel = np.linalg.norm(gg - want) / np.linalg.norm(want)
         rms = np.sqrt(np.mean(want ** 2))
-        elem = np.quantile(np.abs(gg - want).ravel() / (rms + np.abs(want).ravel()), 0.999)
+        elem = np.max(np.abs(gg - want).ravel() / (rms + np.abs(want).ravel()))
         out[name] = (rel, elem)
     return out
 
@@ -93,6 +92,7 @@ def test_adjoint_with_velocities_and_dudt_upstream():
     res = _grad_check(d, v=d["v"], g_du=True)
     for k, (rel, elem) in res.items():
         assert rel <= 1e-3, (k, rel)
+        assert elem <= 1e-3, (k, elem)
 
 
 @pytest.mark.parametrize("cap", [0, 40])
