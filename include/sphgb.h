@@ -242,6 +242,40 @@ int sph_force(sph_ctx* ctx, const float* u, const float* vel, float* acc, float*
 int sph_force_viscous(sph_ctx* ctx, const float* u, const float* vel, float alpha, float c_cfl,
                       float* acc, float* dudt, float* dt, float* balsara, void* stream);
 
+/* One velocity-Verlet time step (Section 4.1: kick-drift-kick with one
+ * global step) of the SPH equations with the artificial viscosity, for ONE
+ * periodic cube [0, box)^3, advancing the caller's state in place:
+ *   a0, du0 = forces at (pos, vel, u)                 (h solved afresh)
+ *   vh = vel + dt/2 a0,  uh = u + dt/2 du0,  pos += dt vh (wrapped)
+ *   a1, du1 = forces at (pos, vh + dt/2 a0, uh + dt/2 du0)
+ *   vel = vh + dt/2 a1,  u = uh + dt/2 du1
+ * where "forces" are Eq. (dvdt) and Eq. (dudt) with the Monaghan-Balsara
+ * terms (sph_force_viscous; alpha = 0 gives the inviscid equations).  The
+ * decomposition is kept from step to step (the pseudo-Verlet reuse of
+ * Section 4.1): a decomposition built for h (1 + slack) serves while twice
+ * the largest displacement since the build stays below the smallest margin
+ * between a particle's cell limit and its h; the sweeps then widen their
+ * axial cutoff and box tests by that amount.  Otherwise, or when a solved h
+ * outgrows the reduced limit, the decomposition is rebuilt from the current
+ * positions.  The first call builds it (h from the density estimate).
+ * Between steps the context keeps the moved positions on that
+ * decomposition: sph_density / sph_force / sph_force_viscous then run on it,
+ * and report SPH_ERR_CELL_LIMIT (instead of rebuilding in place) when a
+ * solved h outgrows it; sph_build starts afresh.
+ *   n        particles (fixed across the steps of one context)
+ *   pos      n x 3 float64 positions, in/out (device)
+ *   vel      n x 3 float32 velocities, in/out;  u  n float32 energies, in/out
+ *   m        n float32 masses
+ *   dt       the step;  alpha, c_cfl  as for sph_force_viscous
+ *   slack    extra cell margin as a fraction of h (0 < slack <= 1; 0.25 is usual)
+ *   dt_min   out (HOST, nullable): the smallest time step of Eq. (dt) at the
+ *            end of the step (evaluated with the predicted velocities)
+ *   rebuilt  out (HOST, nullable): decompositions built during the step
+ * Synchronises `stream`.  The adjoint calls do not cover this step. */
+int sph_verlet_step(sph_ctx* ctx, int64_t n, double* pos, float* vel, float* u, const float* m,
+                    double box, double dt, float alpha, float c_cfl, float slack, float* dt_min,
+                    int32_t* rebuilt, void* stream);
+
 /* Reverse mode of the ghost step and the force loop for a scalar L with
  * upstream gradients g_acc = dL/d acc (n x 3) and g_dudt = dL/d dudt
  * (nullable = 0), at the state of the last sph_force:

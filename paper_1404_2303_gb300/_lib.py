@@ -63,6 +63,9 @@ SIGNATURES = {
     "sph_density": (C.c_int, [P, P, P, P, P, C.POINTER(C.c_int32), P]),
     "sph_force": (C.c_int, [P, P, P, P, P, P, P]),
     "sph_force_viscous": (C.c_int, [P, P, P, C.c_float, C.c_float, P, P, P, P, P]),
+    "sph_verlet_step": (C.c_int, [P, C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_float,
+                                  C.c_float, C.c_float, C.POINTER(C.c_float),
+                                  C.POINTER(C.c_int32), P]),
     "sph_force_adjoint": (C.c_int, [P, P, P, P, P, P, P, P, P, P]),
     "sph_density_adjoint": (C.c_int, [P, P, P, P, P, P, P]),
     "sph_adjoint": (C.c_int, [P, P, P, P, P, P, P, P]),

@@ -12,7 +12,10 @@ namespace {
 constexpr int TPB = 256;
 constexpr float SIGMA = 2.546479089470325f;  // 8/pi
 
-enum : int { HF_ACTIVE = 1, HF_HI_VALID = 2, HF_LIMIT = 4, HF_LO_VALID = 8 };
+enum : int { HF_ACTIVE = 1, HF_HI_VALID = 2, HF_LIMIT = 4, HF_LO_VALID = 8,
+              HF_SIDE = 16,     // the last evaluation moved the lower end
+              HF_RUN1 = 32,     // ... and so did the one before (one-sided run, 2 bits)
+              HF_RUNMASK = 96 };
 
 __global__ void k_fill_mass(long long n, const int* perm, const float* m, float4* pos4) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -39,11 +42,11 @@ __global__ void k_scatter_i(long long n, const int* perm, const int* in, int* ou
   if (s < n) out[perm[s]] = in[s];
 }
 
-__global__ void k_check_h(long long n, const float* h, const float* hlim, int* status) {
+__global__ void k_check_h(long long n, const float* h, const float* hlim, float pad, int* status) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
   float v = h[s];
-  if (!(v > 0.f) || v > hlim[s]) atomicOr(status, ST_CELL_LIMIT);
+  if (!(v > 0.f) || v > hlim[s] - pad) atomicOr(status, ST_CELL_LIMIT);
 }
 
 // ---- smoothing-length solve (Eq. (nneigh)): Newton steps on
@@ -69,6 +72,7 @@ struct HSolve {
   float* dxold;
   int* flag;
   float n_ngb, tol;
+  float pad;       // the cell limit is hlim - pad (particles moved since the build)
   int* nactive;
   int* nlimit;
 };
@@ -79,7 +83,7 @@ struct HSolve {
 __global__ void k_hsolve_init(long long n, HSolve S, int mode) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  const float hl = S.hlim[s];
+  const float hl = S.hlim[s] - S.pad;
   if (mode == 1) {
     const int fl = S.flag[s];
     if (!(fl & HF_LIMIT)) {
@@ -137,10 +141,17 @@ __global__ void k_hsolve_update(long long n, HSolve S) {
   }
   double L = S.lo[s], H = S.hi[s];
   float4 gb = S.gb[s];
-  const double hl = (double)S.hlim[s];
+  const double hl = (double)(S.hlim[s] - S.pad);
   // g(x) = ln N - ln n_ngb and g'(x) = h N'/N in x = ln h
   const float slope = (S.dnngb[s] > 0.f && Nv > 0.f) ? (float)(hd * (double)S.dnngb[s] / (double)Nv) : 0.f;
   const float g = __logf(Nv) - __logf(S.n_ngb);
+  // runs of evaluations on one side of the root (counted up to 3): an
+  // interpolation that keeps landing on the same side is replaced by
+  // bisection, which halves the bracket from that side
+  const int side = f < 0 ? HF_SIDE : 0;
+  int run = (fl & HF_RUNMASK) / HF_RUN1;
+  run = ((fl & HF_SIDE) == side) ? min(run + 1, 3) : 0;
+  fl = (fl & ~(HF_SIDE | HF_RUNMASK)) | side | (run * HF_RUN1);
   if (f < 0) {
     L = hd;
     gb.x = g;
@@ -182,17 +193,22 @@ __global__ void k_hsolve_update(long long n, HSolve S) {
     }
     const double prop = slope > 1e-3f ? hd * (double)__expf(-dx) : -1.0;
     const bool out = !(prop > L && prop < H);
-    const bool slow = fabsf(2.f * g) > fabsf(dxprev * slope);
+    // a step that is not at least twice shorter than the one before gives
+    // way to the bracket (only once both of its ends are evaluated: without
+    // a lower end the fallback would halve h)
+    const bool slow = (fl & HF_LO_VALID) && fabsf(2.f * g) > fabsf(dxprev * slope);
     hn = -1.0;
     if (!(out || slow || slope <= 1e-3f)) {
       hn = prop;
-    } else if ((fl & HF_LO_VALID) && L > 0 && gb.y > 0.f && gb.w > 0.f) {
-      // cubic Hermite interpolation of g over [ln L, ln H]
+    } else if ((fl & HF_LO_VALID) && L > 0 && gb.y > 0.f && gb.w > 0.f && run < 3) {
+      // cubic Hermite interpolation of g over [ln L, ln H]: accurate to the
+      // fourth order in the bracket width, so its root is taken even when it
+      // lies far from the current end (no step-length test)
       const double w = log(H / L);
       const double t = hermite_root((double)gb.x, (double)gb.y * w, (double)gb.z, (double)gb.w * w);
       if (t > 0.0 && t < 1.0) {
         const double q = L * exp(t * w);
-        if (q > L && q < H && fabs(log(q / hd)) <= 0.5f * dxprev) hn = q;
+        if (q > L && q < H) hn = q;
       }
     }
     if (hn > 0) {
@@ -373,6 +389,7 @@ static HSolve hsolve_args(sph_ctx* c, int* nactive, int* nlimit) {
   S.flag = c->h_flag.as<int>();
   S.n_ngb = c->prm.n_ngb;
   S.tol = c->prm.h_tol;
+  S.pad = c->reuse_pad;
   S.nactive = nactive;
   S.nlimit = nlimit;
   return S;
@@ -529,7 +546,10 @@ void sph_destroy(sph_ctx* c) {
                  &c->prof_units, &c->solve_ctl, &c->status, &c->counters, &c->queue, &c->scan_tmp, &c->sort_tmp, &c->tmp_a,
                  &c->tmp_b, &c->tmp_c, &c->p_et, &c->nleaf_dev, &c->n_listed, &c->n_ex, &c->n_lo,
                  &c->n_hi, &c->b_lo, &c->b_hi, &c->fl_list, &c->fl_cnt, &c->fl_flag, &c->fl_blk,
-                 &c->fl_over, &c->task_ctl, &c->tree_ctl, &c->visc4, &c->dt_s};
+                 &c->fl_over, &c->task_ctl, &c->tree_ctl, &c->visc4, &c->dt_s,
+                 &c->b_nseg, &c->u_off, &c->b_part, &c->u_block, &c->u_seg, &c->u_e0, &c->u_e1,
+                 &c->u_key, &c->part, &c->blk_done, &c->vv_acc, &c->vv_du, &c->vv_dt,
+                 &c->vv_vp, &c->vv_up, &c->vv_h, &c->vv_tmp, &c->vv_red};
   for (DBuf* b : all) dbuf_free(*b);
   for (auto& e : c->ev_pending) {
     cudaEventDestroy(e.a);
@@ -553,6 +573,8 @@ int sph_build_batch(sph_ctx* c, int32_t nbox, const int64_t* offsets, const doub
   if (n <= 0 || n >= (1ll << 31) / 16) return SPH_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   ++c->state_gen;
+  if (c->reuse_pad != 0.f) ++c->build_gen;
+  c->reuse_pad = 0.f;
   c->built = c->have_density = c->have_force = false;
   c->fl_valid = false;
   c->have_d2 = 0;
@@ -601,7 +623,7 @@ int sph_density_fixed_h(sph_ctx* c, const float* m, const float* h, float* rho, 
   { k_gather<<<div_up(n, TPB), TPB, 0, s>>>(n, c->perm.as<int>(), h, c->h.as<float>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   { k_check_h<<<div_up(n, TPB), TPB, 0, s>>>(n, c->h.as<float>(), c->hlim.as<float>(),
-                                           c->status.as<int>()); note_launch(); }
+                                           c->reuse_pad, c->status.as<int>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
   SPH_TRY(compute_node_hmax(c, s));
   SPH_TRY(run_sweep(c, PH_DENSITY, 0, count != nullptr, s));
@@ -649,10 +671,47 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
     // nlim accumulates over the whole solve: a particle flagged at its cell
     // limit in any iteration leaves the active set and must trigger the rebuild
     SPH_CUDA(cudaMemsetAsync(nlim, 0, sizeof(int), s));
-    if (c->prm.use_graph && !c->profile) {
-      SPH_TRY(solve_round_graph(c, s, host, &it, total_iters));
+    // The work units were planned from the build's h.  Before each sweep of
+    // the iteration the block costs are estimated again from the current h
+    // of the particles still iterating, and the units re-planned when the
+    // present plan would leave one unit far above its balanced share (the h
+    // of particles next to dense clumps can grow tenfold over the first
+    // iterations, and with it their candidate sets).  While the plan holds,
+    // the rest of the round runs as one device-side graph.
+    bool use_dev = c->prm.use_graph && !c->profile;
+    bool replanned = false;
+    // the first iteration of a fresh decomposition runs on the host, so that
+    // the plan is checked against the h of the first Halley step
+    const int min_host = rebuilds == 0 ? 1 : 0;
+    for (; use_dev && it < c->prm.max_newton;) {
+      bool changed = false;
+      SPH_TRY(replan_units(c, 1, &changed, s));
+      replanned = replanned || changed;
+      if (!changed && !replanned && it >= min_host) break;  // a balanced plan: the graph takes the round
+      SPH_TRY(ensure_state(c));
+      { k_block_active<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, s>>>(
+          c->nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->h_flag.as<int>(),
+          c->blk_active.as<int>()); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+      SPH_TRY(run_sweep(c, PH_DENSITY, 1, 0, s));
+      SPH_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), s));
+      { k_hsolve_update<<<div_up(n, TPB), TPB, 0, s>>>(n, hsolve_args(c, nact, nlim)); note_launch(); }
+      SPH_CUDA(cudaGetLastError());
+      SPH_CUDA(cudaMemcpyAsync(host, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      SPH_CUDA(cudaStreamSynchronize(s));
+      if (total_iters + it < 32) c->stats.newton_active[total_iters + it] = host[0];
+      ++it;
+      if (host[0] == 0) break;
+    }
+    if (host[0] == 0) {
+      // converged on the host iterations
+    } else if (use_dev) {
+      int itg = 0;
+      SPH_TRY(solve_round_graph(c, s, host, &itg, total_iters + it));
+      it += itg;
     } else {
     for (; it < c->prm.max_newton; ++it) {
+      SPH_TRY(replan_units(c, 1, nullptr, s));
       { k_block_active<<<div_up((long long)c->nblock * 32, TPB), TPB, 0, s>>>(
           c->nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->h_flag.as<int>(),
           c->blk_active.as<int>()); note_launch(); }
@@ -677,7 +736,10 @@ int sph_density(sph_ctx* c, const float* m, float* h_out, float* rho, float* ome
       return SPH_ERR_H_NOT_CONVERGED;
     }
     if (host[1] == 0) break;
-    if (rebuilds >= c->prm.max_rebuild) {
+    // positions moved since the build (velocity-Verlet steps) leave the
+    // Morton order and build-time positions that an in-place rebuild uses
+    // stale: only a full sph_build from the current positions can help
+    if (rebuilds >= c->prm.max_rebuild || c->reuse_pad > 0.f) {
       c->stats.newton_iters = total_iters;
       return SPH_ERR_CELL_LIMIT;
     }
@@ -736,6 +798,7 @@ int sph_force(sph_ctx* c, const float* u, const float* vel, float* acc, float* d
                                          c->u_s.as<float>(), c->vel4.as<float4>(),
                                          c->fdat.as<float4>()); note_launch(); }
   SPH_CUDA(cudaGetLastError());
+  SPH_TRY(replan_units(c, 0, nullptr, s));  // the units for the solved h of every particle
   SPH_TRY(run_sweep(c, PH_FORCE, 0, count != nullptr, s));
   { k_scatter_acc<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->acc4.as<float4>(), acc, dudt); note_launch(); }
   SPH_CUDA(cudaGetLastError());
@@ -770,6 +833,7 @@ int sph_force_viscous(sph_ctx* c, const float* u, const float* vel, float alpha,
   SPH_CUDA(cudaGetLastError());
   c->visc_alpha = alpha;
   c->visc_cfl = c_cfl;
+  SPH_TRY(replan_units(c, 0, nullptr, s));
   SPH_TRY(run_sweep(c, PH_VELDERIV, 0, 0, s));
   SPH_TRY(run_sweep(c, PH_FORCE_VISC, 0, 0, s));
   { k_scatter_acc<<<div_up(n, TPB), TPB, 0, s>>>(n, perm, c->acc4.as<float4>(), acc, dudt); note_launch(); }

@@ -775,6 +775,111 @@ __global__ void k_block_dts(int nblock, const int* b_leaf, const int* b_count, c
   cost[b] = (unsigned long long)(0xffffffffu - cc);  // ascending key = descending cost
 }
 
+// ---------------------------------------------------------------- work units
+// A block whose sweep is long (a leaf next to a dense clump: its large-h
+// particles reach 10^5 neighbours or more, so one warp would gather them
+// serially for tens of milliseconds) is swept by several work units, each
+// over a contiguous slice of its interaction list; the slices' partial sums
+// are added, in slice order, by the unit that finishes last (see k_sweep).
+// The sweep cost of a block is estimated as its chunks times the candidates
+// its targets can contribute: each target's particle count (at most 4096)
+// times the fraction of the target's particle box that lies within reach of
+// the block's box grown by its largest h (a target wholly within reach
+// contributes all its particles, a far one none).
+__device__ __forceinline__ float overlap1(float lo, float hi, float a, float b) {
+  const float w = hi - lo;
+  const float o = fminf(hi, b) - fmaxf(lo, a);
+  return w > 0.f ? fminf(fmaxf(o / w, 0.f), 1.f) : (lo >= a && lo <= b ? 1.f : 0.f);
+}
+
+__global__ void k_block_cost(int nblock, const int* b_first, const int* b_count,
+                             const long long* dtoff, const int* dt_cj, const float4* dt_shift,
+                             const float* h, const int* pflag, const int* ncount,
+                             const float4* n_lo, const float4* n_hi, const float4* b_lo,
+                             const float4* b_hi, const int* nseg, unsigned long long* cost,
+                             unsigned long long* total, unsigned long long* maxc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblock) return;
+  const int f = b_first[b], bn0 = b_count[b];
+  float hm = 0.f;
+  int bn = 0;  // particles to sweep (pflag: only those still iterating)
+  for (int k = 0; k < bn0; ++k) {
+    if (pflag && !(pflag[f + k] & 1)) continue;
+    hm = fmaxf(hm, h[f + k]);
+    ++bn;
+  }
+  if (bn == 0) {
+    cost[b] = 0;
+    return;
+  }
+  const float4 l0 = b_lo[b], h0 = b_hi[b];
+  double w = bn;
+  for (long long e = dtoff[b]; e < dtoff[b + 1]; ++e) {
+    const int cj = dt_cj[e];
+    const float4 sh = dt_shift[e];
+    int nt;
+    float4 tl, th;
+    if (cj >= 0) {
+      nt = ncount[cj];
+      tl = n_lo[cj];
+      th = n_hi[cj];
+    } else {
+      nt = b_count[-1 - cj];
+      tl = b_lo[-1 - cj];
+      th = b_hi[-1 - cj];
+    }
+    const float fr = overlap1(tl.x + sh.x, th.x + sh.x, l0.x - hm, h0.x + hm) *
+                     overlap1(tl.y + sh.y, th.y + sh.y, l0.y - hm, h0.y + hm) *
+                     overlap1(tl.z + sh.z, th.z + sh.z, l0.z - hm, h0.z + hm);
+    w += (double)min(nt, 4096) * fr;
+  }
+  w *= (double)((bn + 31) / 32);
+  const unsigned long long c = (unsigned long long)fmin(w, 4.0e9);
+  cost[b] = c;
+  atomicAdd(total, c);
+  // the largest unit of the present plan (its slices share the cost)
+  if (maxc) atomicMax(maxc, c / (unsigned long long)max(1, nseg ? nseg[b] : 1));
+}
+
+// slices per block: the cost over four times the mean block cost, at most
+// one slice per 8 interaction entries
+__global__ void k_block_nseg(int nblock, const long long* dtoff, const unsigned long long* cost,
+                             const unsigned long long* total, int* nseg) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblock) return;
+  const double unit = 4.0 * (double)(*total) / (double)nblock + 1.0;
+  const long long ent = dtoff[b + 1] - dtoff[b];
+  const long long k = (long long)ceil((double)cost[b] / unit);
+  nseg[b] = (int)max(1ll, min(k, ent / 8));
+}
+
+__global__ void k_block_partsz(int nblock, const int* nseg, const int* bcount, long long* psz) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblock) return;
+  psz[b] = nseg[b] > 1 ? (long long)nseg[b] * bcount[b] * SPH_PART_STRIDE : 0;
+}
+
+__global__ void k_make_units(int nblock, const int* nseg, const int* uoff, const long long* dtoff,
+                             const unsigned long long* cost, int* u_block, int* u_seg,
+                             long long* u_e0, long long* u_e1, unsigned long long* ukey, int* uid) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblock) return;
+  const int ns = nseg[b], base = uoff[b];
+  const long long e0 = dtoff[b], e1 = dtoff[b + 1];
+  const long long S = (e1 - e0 + ns - 1) / ns;
+  const unsigned long long cu = cost[b] / (unsigned long long)ns;
+  const unsigned cc = cu > 0xffffffffull ? 0xffffffffu : (unsigned)cu;
+  for (int k = 0; k < ns; ++k) {
+    const int u = base + k;
+    u_block[u] = b;
+    u_seg[u] = k;
+    u_e0[u] = min(e1, e0 + k * S);
+    u_e1[u] = (k == ns - 1) ? e1 : min(e1, e0 + (k + 1) * S);
+    ukey[u] = (unsigned long long)(0xffffffffu - cc);  // ascending = costliest first
+    uid[u] = u;
+  }
+}
+
 __global__ void k_iota(int n, int* v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = i;
@@ -1435,6 +1540,97 @@ static int build_tasks(sph_ctx* c, cudaStream_t s) {
   return SPH_OK;
 }
 
+// Work units from per-block costs (device): slices per block, unit arrays,
+// partial-sum offsets, and the LPT order.  One host read of the unit and
+// partial-sum counts.
+static int make_plan(sph_ctx* c, const unsigned long long* bc, const unsigned long long* tot,
+                     cudaStream_t s) {
+  const int nblock = c->nblock;
+  SPH_TRY(dbuf_ensure(c->b_nseg, sizeof(int) * (nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->u_off, sizeof(int) * (nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->b_part, sizeof(long long) * (nblock + 1)));
+  SPH_TRY(dbuf_ensure(c->tmp_b, sizeof(long long) * (nblock + 1)));
+  int* nseg = c->b_nseg.as<int>();
+  { k_block_nseg<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, c->b_dtoff.as<long long>(), bc, tot,
+                                                     nseg); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(scan_exclusive_i32(nseg, c->u_off.as<int>(), nblock, c->u_off.as<int>() + nblock,
+                             c->scan_tmp, s));
+  { k_block_partsz<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, nseg, c->b_count.as<int>(),
+                                                       c->tmp_b.as<long long>()); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(scan_exclusive_i64(c->tmp_b.as<long long>(), c->b_part.as<long long>(), nblock,
+                             c->b_part.as<long long>() + nblock, c->scan_tmp, s));
+  int nunits = 0;
+  long long npart = 0;
+  SPH_TRY(d2h(&nunits, c->u_off.as<int>() + nblock, s));
+  SPH_TRY(d2h(&npart, c->b_part.as<long long>() + nblock, s));
+  c->nunits = nunits;
+  SPH_TRY(dbuf_ensure(c->u_block, sizeof(int) * (nunits + 1)));
+  SPH_TRY(dbuf_ensure(c->u_seg, sizeof(int) * (nunits + 1)));
+  SPH_TRY(dbuf_ensure(c->u_e0, sizeof(long long) * (nunits + 1)));
+  SPH_TRY(dbuf_ensure(c->u_e1, sizeof(long long) * (nunits + 1)));
+  SPH_TRY(dbuf_ensure(c->u_key, sizeof(unsigned long long) * (nunits + 1) * 2));
+  SPH_TRY(dbuf_ensure(c->b_order, sizeof(int) * (nunits + 1) * 2));
+  SPH_TRY(dbuf_ensure(c->part, sizeof(float) * (size_t)(npart + 1)));
+  SPH_TRY(dbuf_ensure(c->blk_done, sizeof(int) * (nblock + 1)));
+  SPH_CUDA(cudaMemsetAsync(c->blk_done.p, 0, sizeof(int) * (nblock + 1), s));
+  unsigned long long* uk = c->u_key.as<unsigned long long>();
+  int* ov = c->b_order.as<int>();
+  { k_make_units<<<div_up(nblock, TPB), TPB, 0, s>>>(
+      nblock, nseg, c->u_off.as<int>(), c->b_dtoff.as<long long>(), bc, c->u_block.as<int>(),
+      c->u_seg.as<int>(), c->u_e0.as<long long>(), c->u_e1.as<long long>(), uk, ov); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  SPH_TRY(radix_sort_u64(uk, ov, uk + (nunits + 1), ov + (nunits + 1), nunits, 32, c->sort_tmp, s));
+  ++c->build_gen;  // captured graphs hold the unit arrays and counts
+  return SPH_OK;
+}
+
+// block costs of the next sweep, estimated with the current h (into the
+// second half of b_cost); total and the largest unit of the present plan
+static int estimate_costs(sph_ctx* c, const int* pflag, const float* h, const int* nseg,
+                          cudaStream_t s) {
+  const int nblock = c->nblock;
+  SPH_TRY(dbuf_ensure(c->b_cost, sizeof(unsigned long long) * (nblock + 1) * 2));
+  SPH_TRY(dbuf_ensure(c->plan_max, 64));
+  unsigned long long* bc = c->b_cost.as<unsigned long long>() + (nblock + 1);
+  unsigned long long* tot = c->plan_max.as<unsigned long long>();
+  SPH_CUDA(cudaMemsetAsync(tot, 0, 2 * sizeof(unsigned long long), s));
+  { k_block_cost<<<div_up(nblock, TPB), TPB, 0, s>>>(
+      nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->b_dtoff.as<long long>(),
+      c->dt_cj.as<int>(), c->dt_shift.as<float4>(), h, pflag, c->n_count.as<int>(),
+      c->n_lo.as<float4>(), c->n_hi.as<float4>(), c->b_lo.as<float4>(), c->b_hi.as<float4>(), nseg,
+      bc, tot, tot + 1); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  return SPH_OK;
+}
+
+int replan_units(sph_ctx* c, int only_active, bool* changed, cudaStream_t s) {
+  if (changed) *changed = false;
+  const int nblock = c->nblock;
+  if (nblock == 0) return SPH_OK;
+  SPH_TRY(estimate_costs(c, only_active ? c->h_flag.as<int>() : nullptr, c->h.as<float>(),
+                         c->b_nseg.as<int>(), s));
+  unsigned long long host[2];
+  SPH_CUDA(cudaMemcpyAsync(host, c->plan_max.p, sizeof(host), cudaMemcpyDeviceToHost, s));
+  SPH_CUDA(cudaStreamSynchronize(s));
+  // balanced share of one resident warp; keep the plan while its largest
+  // unit stays within four such shares
+  int nsm = c->sweep_grid;
+  if (nsm <= 0) {  // no sweep launched yet: two CTAs per SM
+    int dev = 0;
+    SPH_CUDA(cudaGetDevice(&dev));
+    SPH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    nsm *= 2;
+  }
+  const double warps = (double)nsm * std::max(1, c->prm.warps_per_cta);
+  if ((double)host[1] <= 4.0 * (double)host[0] / warps + 1.0) return SPH_OK;
+  const unsigned long long* bc = c->b_cost.as<unsigned long long>() + (nblock + 1);
+  SPH_TRY(make_plan(c, bc, c->plan_max.as<unsigned long long>(), s));
+  if (changed) *changed = true;
+  return SPH_OK;
+}
+
 static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
   const int ncell = c->ncell;
   const long long n = c->n;
@@ -1597,11 +1793,6 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
       listed, c->n_child0.as<int>(), nblk, blk0, c->b_dtoff.as<long long>(), c->dt_cj.as<int>(),
       c->dt_code.as<int>(), c->dt_shift.as<float4>(), ck); note_launch(); }
   SPH_CUDA(cudaGetLastError());
-  // LPT order: descending cost, ties by block id (the sort is stable)
-  int* ov = c->b_order.as<int>();
-  { k_iota<<<div_up(nblock, TPB), TPB, 0, s>>>(nblock, ov); note_launch(); }
-  SPH_CUDA(cudaGetLastError());
-  SPH_TRY(radix_sort_u64(ck, ov, ck + (nblock + 1), ov + (nblock + 1), nblock, 32, c->sort_tmp, s));
   // leaves (nodes with blocks), counted on the device; read with the statistics
   SPH_TRY(dbuf_ensure(c->nleaf_dev, 64));
   SPH_CUDA(cudaMemsetAsync(c->nleaf_dev.p, 0, sizeof(int), s));
@@ -1692,6 +1883,15 @@ int build_from_guess(sph_ctx* c, cudaStream_t s) {
                            cudaMemcpyDeviceToDevice, s));
   SPH_TRY(compute_node_hmax(c, s));
   SPH_TRY(compute_bboxes(c, s));
+  // work units: blocks whose estimated sweep cost exceeds four times the
+  // mean are cut into slices of their interaction lists; LPT order of the
+  // units by estimated cost (re-planned with the current h before the
+  // sweeps of the h solve and of the force when it has drifted)
+  {
+    SPH_TRY(estimate_costs(c, nullptr, c->hguess.as<float>(), nullptr, s));
+    SPH_TRY(make_plan(c, c->b_cost.as<unsigned long long>() + (c->nblock + 1),
+                      c->plan_max.as<unsigned long long>(), s));
+  }
   SPH_TRY(build_mark(c, s, 7));
   return SPH_OK;
 }

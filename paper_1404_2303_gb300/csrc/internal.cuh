@@ -12,6 +12,7 @@
 #define SPH_MAX_BOX 1024
 #define SPH_NDIR 13
 #define SPH_SELF_DIR 0  // self interactions sweep along sort direction 0 (the z axis)
+#define SPH_PART_STRIDE 8  // floats per (work unit, particle) partial: the sums and a count
 
 // ---------------------------------------------------------------------------
 // error handling: every CUDA call is checked and mapped to SPH_ERR_CUDA
@@ -81,6 +82,12 @@ struct sph_ctx {
   std::vector<int> top_base;       // first top-cell node per box (nbox+1)
   bool built = false;
   long long state_gen = 0;  // bumped by every call that replaces the forward state
+  // positions moved since the build without rebuilding (velocity-Verlet
+  // steps): twice the largest displacement, added to the sweeps' axial and
+  // box margins and taken off the cell limits of the h solve
+  float reuse_pad = 0.f;
+  bool vv_ready = false;    // vv_h holds the smoothing lengths of the last step
+  DBuf vv_acc, vv_du, vv_dt, vv_vp, vv_up, vv_h, vv_tmp, vv_red;
   bool have_density = false;
   bool have_force = false;
   int have_d2 = 0;
@@ -129,6 +136,11 @@ struct sph_ctx {
   int64_t ndt = 0;
   DBuf b_first, b_count, b_leaf, b_dtoff, b_order, b_cost, b_hmax;
   DBuf b_lo, b_hi;  // float4 particle bounding box of the block
+  // work units: slices of the blocks' interaction lists (b_order holds the
+  // units in LPT order); partial sums of blocks cut into several units
+  int nunits = 0;
+  DBuf b_nseg, u_off, b_part, u_block, u_seg, u_e0, u_e1, u_key, part, blk_done;
+  DBuf plan_max;     // unsigned long long: largest estimated block cost of the last estimate
   DBuf dt_cj;      // int
   DBuf dt_code;    // int: dir | (sgn+1) << 8
   DBuf dt_shift;   // float4 (sx, sy, sz, 0)
@@ -219,6 +231,11 @@ int build_from_guess(sph_ctx* c, cudaStream_t s);
 int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t s);
 int set_dir_table(sph_ctx* c);  // the 13 sort directions into constant memory (once)
 int compute_node_hmax(sph_ctx* c, cudaStream_t s);
+// re-plan the work units from block costs estimated with the current h
+// (only_active: the particles still iterating in the h solve) when the
+// present plan would leave one unit well above the balanced share of the
+// resident warps; *changed tells whether it did
+int replan_units(sph_ctx* c, int only_active, bool* changed, cudaStream_t s);
 
 // sweep phases
 enum : int {

@@ -64,8 +64,17 @@ __device__ __forceinline__ unsigned make_tag(int j, float sx, float sy, float sz
 
 struct SweepArgs {
   int nblock;
+  int nunits;           // work units (slices of the blocks' interaction lists)
   int cap;  // buffered j-particles per warp between two compute passes
-  const int* order;
+  const int* order;     // units in LPT order
+  const int* u_block;   // unit -> block, slice index and entry range
+  const int* u_seg;
+  const long long* u_e0;
+  const long long* u_e1;
+  const int* b_nseg;    // slices per block
+  const long long* b_part;  // partial-sum base of a block cut into slices (floats)
+  float* part;
+  int* blk_done;        // slices of the block finished in this launch
   const int* b_first;
   const int* b_count;
   const long long* b_dtoff;
@@ -139,6 +148,7 @@ struct SweepArgs {
 // ---------------------------------------------------------------------------
 struct PDensity {
   static constexpr int NACC = 5;
+  static constexpr int MINB = 3;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 1;
   static constexpr bool WRITES = false;
@@ -204,6 +214,7 @@ struct PDensity {
 // d^2 rho / dh^2 = sigma/h^5 sum m (12 w + 8 q w' + q^2 w''), w'' = 12 (a - 4b)
 struct PDensityD2 {
   static constexpr int NACC = 1;
+  static constexpr int MINB = 3;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 1;
   static constexpr bool WRITES = false;
@@ -248,6 +259,7 @@ struct PDensityD2 {
 // ---------------------------------------------------------------------------
 struct PForce {
   static constexpr int NACC = 4;
+  static constexpr int MINB = 2;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 3;
   static constexpr bool WRITES = true;  // records the pair lists
@@ -332,6 +344,7 @@ struct PForce {
 // ---------------------------------------------------------------------------
 struct PForceAdj {
   static constexpr int NACC = 6;  // gx, gy, gz, gm, gA, gh
+  static constexpr int MINB = 2;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 4;
   static constexpr bool WRITES = false;
@@ -429,6 +442,7 @@ struct PForceAdj {
 // ---------------------------------------------------------------------------
 struct PDensityAdj {
   static constexpr int NACC = 4;  // gx, gy, gz, gm
+  static constexpr int MINB = 3;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 3;
   static constexpr bool WRITES = false;
@@ -499,6 +513,7 @@ struct PDensityAdj {
 // ---------------------------------------------------------------------------
 struct PVelDeriv {
   static constexpr int NACC = 4;  // div, curl x, y, z
+  static constexpr int MINB = 2;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 0;
   static constexpr int JW = 2;
   static constexpr bool USES_HJ = false;
@@ -569,6 +584,7 @@ struct PVelDeriv {
 // ---------------------------------------------------------------------------
 struct PForceVisc {
   static constexpr int NACC = 6;  // a (3), du pressure, du viscous, max signal speed
+  static constexpr int MINB = 2;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 1;
   static constexpr int JW = 4;
   static constexpr bool USES_HJ = true;
@@ -660,6 +676,7 @@ struct PForceVisc {
 template <int FORCE>
 struct PDump {
   static constexpr int NACC = 1;
+  static constexpr int MINB = 3;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 2;
   static constexpr bool WRITES = false;
@@ -829,8 +846,50 @@ __host__ __device__ __forceinline__ int warp_smem_f4(int cap, int bmax) {
   return cap * P::JW + 32 + bmax / 4 + (LIST ? cap * 2 : 0);
 }
 
+// The slice of a block cut into several work units that finishes last adds
+// the partial sums of all slices in slice order (deterministic whatever the
+// finishing order) and finalises; its counter returns to zero for the next
+// launch.  No unit waits for another.  (Kept out of line: it runs once per
+// sliced block and would otherwise add registers to the whole sweep.)
 template <class P, bool COUNT, bool LIST>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+__device__ __noinline__ void combine_slices(const SweepArgs& a, int b, int bf, int bn, int nseg) {
+  const int lane = threadIdx.x & 31;
+  __threadfence();
+  __syncwarp();
+  int last = 0;
+  if (lane == 0) last = atomicAdd(a.blk_done + b, 1) == nseg - 1;
+  last = __shfl_sync(FULL, last, 0);
+  if (!last) return;
+  __threadfence();
+  for (int k = lane; k < bn; k += 32) {
+    const int p = bf + k;
+    if (a.pflag && !(a.pflag[p] & 1)) continue;  // not swept in this launch
+    float v[P::NACC];
+    int cg = 0;
+    for (int sg = 0; sg < nseg; ++sg) {
+      const float* pp = a.part + a.b_part[b] + ((size_t)sg * bn + k) * SPH_PART_STRIDE;
+#pragma unroll
+      for (int kk = 0; kk < P::NACC; ++kk) {
+        const float x = __ldcg(pp + kk);
+        v[kk] = sg == 0 ? x : (kk >= P::NACC - P::NMAX ? fmaxf(v[kk], x) : v[kk] + x);
+      }
+      cg += __float_as_int(__ldcg(pp + P::NACC));
+    }
+    P::finalize(a, p, v);
+    if (COUNT && a.ocnt) a.ocnt[p] = cg;
+    if (P::WRITES && LIST && a.fl_list) {  // no list for a sliced block: swept later
+      a.fl_cnt[p] = -1;
+      a.fl_flag[p] = 1;
+      atomicAdd(a.fl_over, 1);
+      a.fl_blk[b] = 1;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) a.blk_done[b] = 0;
+}
+
+template <class P, bool COUNT, bool LIST>
+__global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
   extern __shared__ float4 smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cap = a.cap;
@@ -844,11 +903,15 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     int q = 0;
     if (lane == 0) q = atomicAdd(a.queue, 1);
     q = __shfl_sync(FULL, q, 0);
-    if (q >= a.nblock) break;
-    const int b = a.order[q];
+    if (q >= a.nunits) break;
+    const int un = a.order[q];
+    const int b = a.u_block[un];
     if (a.blk_active && a.blk_active[b] == 0) continue;
     const int bf = a.b_first[b], bn = a.b_count[b];
-    const long long e0 = a.b_dtoff[b], e1 = a.b_dtoff[b + 1];
+    // this unit's slice of the block's interaction list; a block cut into
+    // several slices leaves partial sums for the last slice to finish
+    const int seg = a.u_seg[un], nseg = a.b_nseg[b];
+    const long long e0 = a.u_e0[un], e1 = a.u_e1[un];
     // The block's particles are swept grouped by h class (factor-2 bands
     // above the block's smallest h, Morton order inside a band): chunks share
     // one window per task, set by their largest h, so a few large-h particles
@@ -904,7 +967,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 #pragma unroll
       for (int k = 0; k < P::NACC; ++k) acc[k] = cmp[k] = part[k] = 0.f;
       int cnt = 0, ncand = 0, staged = 0, wtot = 0;
-      unsigned* wl = (P::WRITES && LIST && a.fl_list && vi)
+      unsigned* wl = (P::WRITES && LIST && a.fl_list && vi && nseg == 1)
                          ? a.fl_list + ((size_t)(pi >> 5) * a.fl_K) * 32 + (pi & 31)
                          : nullptr;
       for (long long g = e0; g < e1; g += 32) {
@@ -1049,7 +1112,14 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           cg += __shfl_xor_sync(FULL, cg, o);
         }
       }
-      if (vi && sub == 0) {
+      if (nseg > 1) {
+        if (vi && sub == 0) {
+          float* pp = a.part + a.b_part[b] + ((size_t)seg * bn + (pi - bf)) * SPH_PART_STRIDE;
+#pragma unroll
+          for (int k = 0; k < P::NACC; ++k) pp[k] = v[k];
+          pp[P::NACC] = __int_as_float(cg);
+        }
+      } else if (vi && sub == 0) {
         P::finalize(a, pi, v);
         if (COUNT && a.ocnt) a.ocnt[pi] = cg;
         if (wl) {
@@ -1077,6 +1147,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       __syncwarp();
     }
     }
+    if (nseg > 1) combine_slices<P, COUNT, LIST>(a, b, bf, bn, nseg);
   }
 }
 
@@ -1095,7 +1166,7 @@ int launch_shape(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
     if (per_sm <= 0) per_sm = 1;
   }
   int grid = nsm * per_sm;
-  int maxgrid = div_up(a.nblock, warps);
+  int maxgrid = div_up(a.nunits, warps);
   if (grid > maxgrid) grid = maxgrid > 0 ? maxgrid : 1;
   c->sweep_grid = grid;
   c->sweep_threads = 32 * warps;
@@ -1316,7 +1387,16 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   SPH_TRY(set_dir_table(c));
   SweepArgs a{};
   a.nblock = c->nblock;
+  a.nunits = c->nunits;
   a.order = c->b_order.as<int>();
+  a.u_block = c->u_block.as<int>();
+  a.u_seg = c->u_seg.as<int>();
+  a.u_e0 = c->u_e0.as<long long>();
+  a.u_e1 = c->u_e1.as<long long>();
+  a.b_nseg = c->b_nseg.as<int>();
+  a.b_part = c->b_part.as<long long>();
+  a.part = c->part.as<float>();
+  a.blk_done = c->blk_done.as<int>();
   a.b_first = c->b_first.as<int>();
   a.b_count = c->b_count.as<int>();
   a.b_dtoff = c->b_dtoff.as<long long>();
@@ -1343,7 +1423,10 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   a.status = c->status.as<int>();
   double emax = 0;
   for (int b = 0; b < c->nbox; ++b) emax = std::max(emax, c->box_L[b] / (double)(1 << c->box_t[b]));
-  a.delta = (float)(emax * (1.0 / 65536.0));
+  // margin of the axial cutoff and the box tests: the rounding of the FP32
+  // keys and shifts, plus twice the largest displacement since the build
+  // when positions were moved without rebuilding (stale keys and boxes)
+  a.delta = (float)(emax * (1.0 / 65536.0)) + c->reuse_pad;
   a.kahan = c->prm.kahan ? 1 : 0;
   a.naive = c->prm.sorted_sweep ? 0 : 1;
   a.ocnt = counting ? c->cnt_i.as<int>() : nullptr;

@@ -151,6 +151,28 @@ class SPH:
               "sph_force_viscous")
         return acc, dudt, dt, f
 
+    # -- time integration -----------------------------------------------------
+    def verlet_step(self, pos, vel, u, m, dt, box=1.0, alpha=0.8, c_cfl=0.25, slack=0.25):
+        """One velocity-Verlet step (Section 4.1), in place on pos (N,3)
+        float64, vel (N,3) float32 and u (N,) float32 device tensors (they
+        must be contiguous of those dtypes).  Returns (dt_min, rebuilt): the
+        smallest Eq. (dt) step at the end of the step and the number of
+        decompositions built."""
+        for t, dt_, shp in ((pos, torch.float64, 2), (vel, torch.float32, 2), (u, torch.float32, 1)):
+            if t.dtype != dt_ or not t.is_contiguous() or not t.is_cuda or t.dim() != shp:
+                raise ValueError("verlet_step updates pos/vel/u in place: contiguous CUDA tensors "
+                                 "of dtype float64 / float32 / float32")
+        m = _f32(m)
+        n = pos.shape[0]
+        dtm = C.c_float(0.0)
+        nb = C.c_int32(0)
+        check(self.lib.sph_verlet_step(self.h, n, _ptr(pos), _ptr(vel), _ptr(u), _ptr(m),
+                                       float(box), float(dt), float(alpha), float(c_cfl),
+                                       float(slack), C.byref(dtm), C.byref(nb), _stream()),
+              "sph_verlet_step")
+        self.n = n
+        return float(dtm.value), int(nb.value)
+
     # -- adjoints ------------------------------------------------------------
     def force_adjoint(self, g_acc, g_dudt=None):
         g_acc = _f32(g_acc, (self.n, 3))
