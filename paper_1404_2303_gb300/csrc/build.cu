@@ -1047,6 +1047,20 @@ __global__ void k_merge_count(int g0, int g1, const int* need, const int* child0
   segs[node - g0] = mergeable(node, need, child0, nblk, count, listed) ? __popc(need[node]) : 0;
 }
 
+// segment table: the node and the direction of every (node, direction)
+// merge segment, so that a merge CTA finds its work without a search
+__global__ void k_merge_fill(int ncell, const int* need, const int* child0, const int* nblk,
+                             const int* count, const int* listed, const long long* sgo,
+                             int* seg_node, unsigned char* seg_dir) {
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= ncell || !mergeable(node, need, child0, nblk, count, listed)) return;
+  long long k = sgo[node];
+  for (int nd = need[node]; nd; nd &= nd - 1, ++k) {
+    seg_node[k] = node;
+    seg_dir[k] = (unsigned char)(__ffs(nd) - 1);
+  }
+}
+
 __device__ __forceinline__ int count_less_s(const float* k, const int* ix, int n, float kv, int iv) {
   int lo = 0, hi = n;
   while (lo < hi) {
@@ -1060,7 +1074,7 @@ __device__ __forceinline__ int count_less_s(const float* k, const int* ix, int n
 // leaf's blocks' lists of that direction) are loaded side by side into
 // shared memory and every element is ranked against the other sub-lists
 __global__ void __launch_bounds__(MS_TPB)
-    k_merge_smem(int g0, int ng, const long long* soff, long long seg0, const int* need,
+    k_merge_smem(long long seg0, const int* seg_node, const unsigned char* seg_dir,
                  const int* child0, const int* count, const int* nblk, const int* blk0,
                  const int* b_first, const int* b_count, const long long* sbase, float* s_key,
                  int* s_idx) {
@@ -1070,39 +1084,43 @@ __global__ void __launch_bounds__(MS_TPB)
   __shared__ long long sb[MS_SUB];
   __shared__ long long dst0;
   __shared__ int nsub_s;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // the first warp reads the sub-lists' sizes and bases in parallel and
+    // scans them into offsets
+    const int lane = threadIdx.x;
     const long long sg = seg0 + blockIdx.x;
-    int lo = 0, hi = ng;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (soff[mid] <= sg) lo = mid; else hi = mid;
-    }
-    const int node = g0 + lo;
-    int nd = need[node];
-    for (long long k = sg - soff[lo]; k > 0; --k) nd &= nd - 1;
-    const int d = __ffs(nd) - 1;
+    const int node = seg_node[sg];
+    const int d = seg_dir[sg];
     const bool leaf = child0[node] < 0;
     const int nsub = leaf ? nblk[node] : 8;
-    int acc = 0;
-    for (int q = 0; q < nsub; ++q) {
-      int sc;
-      long long base;
+    int sc = 0;
+    long long base = 0;
+    if (lane < nsub) {
       if (leaf) {
-        const int bi = blk0[node] + q;
+        const int bi = blk0[node] + lane;
         sc = b_count[bi];
         base = 13ll * b_first[bi] + (long long)d * sc;
       } else {
-        const int ch = child0[node] + q;
+        const int ch = child0[node] + lane;
         sc = count[ch];
         base = sc > 0 ? sbase[ch] + (long long)d * sc : 0;
       }
-      so[q] = acc;
-      sb[q] = base;
-      acc += sc;
     }
-    so[nsub] = acc;
-    nsub_s = nsub;
-    dst0 = sbase[node] + (long long)d * count[node];
+    int incl = sc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane < nsub) {
+      so[lane] = incl - sc;
+      sb[lane] = base;
+    }
+    if (lane == nsub - 1) so[nsub] = incl;
+    if (lane == 0) {
+      nsub_s = nsub;
+      dst0 = sbase[node] + (long long)d * count[node];
+    }
   }
   __syncthreads();
   const int nsub = nsub_s;
@@ -1735,16 +1753,27 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
     std::vector<long long> goff(ngen);
     SPH_CUDA(cudaMemcpyAsync(goff.data(), gofs, sizeof(long long) * ngen, cudaMemcpyDeviceToHost, s));
     SPH_CUDA(cudaStreamSynchronize(s));
+    const long long nseg_all = goff[ngen - 1];  // gen_start ends with the node count
+    DBuf segtab;
+    SPH_TRY(dbuf_ensure(segtab, (size_t)(nseg_all + 1) * 5 + 16));
+    int* seg_node = segtab.as<int>();
+    unsigned char* seg_dir = reinterpret_cast<unsigned char*>(seg_node + nseg_all + 1);
+    { k_merge_fill<<<div_up(ng_all, TPB), TPB, 0, s>>>(ng_all, need, c->n_child0.as<int>(), nblk,
+                                                       c->n_count.as<int>(), listed, sgo, seg_node,
+                                                       seg_dir); note_launch(); }
+    SPH_CUDA(cudaGetLastError());
     for (int g = ngen - 2; g >= 0; --g) {
       const int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
       const long long nseg = goff[g + 1] - goff[g];
       if (g1 <= g0 || nseg <= 0) continue;
       { k_merge_smem<<<(unsigned)nseg, MS_TPB, 0, s>>>(
-          g0, g1 - g0, sgo + g0, goff[g], need, c->n_child0.as<int>(), c->n_count.as<int>(), nblk,
-          blk0, c->b_first.as<int>(), c->b_count.as<int>(), c->n_sbase.as<long long>(),
+          goff[g], seg_node, seg_dir, c->n_child0.as<int>(), c->n_count.as<int>(), nblk, blk0,
+          c->b_first.as<int>(), c->b_count.as<int>(), c->n_sbase.as<long long>(),
           c->s_key.as<float>(), c->s_idx.as<int>()); note_launch(); }
       SPH_CUDA(cudaGetLastError());
     }
+    SPH_CUDA(cudaStreamSynchronize(s));  // the table is freed below
+    dbuf_free(segtab);
   }
   dbuf_free(sz);
   SPH_TRY(build_mark(c, s, 5));
