@@ -3,8 +3,8 @@ the Sedov-blast setup, Section 4.2) by properties the equations fix but the
 integration does not impose: mass conservation (the swept-up gas is all
 inside the shock), the central asymptotics U/eta -> 1/gamma,
 G ~ eta^(3/(gamma-1)) and a pressure plateau (from the leading-order
-balance of the similarity equations), and the released energy recovered
-from the dimensional solution."""
+balance of the similarity equations), the released energy recovered
+from the dimensional solution, and the published shock-radius constants."""
 import math
 
 import numpy as np
@@ -41,3 +41,14 @@ def test_energy_of_the_dimensional_solution():
     inside = r < R
     m = np.trapezoid((rho * 4.0 * math.pi * r * r)[inside], r[inside])
     assert abs(m / (4.0 / 3.0 * math.pi * R ** 3 * rho0) - 1.0) < 2e-3
+
+
+@pytest.mark.parametrize("gamma,alpha", [(1.4, 0.851), (5.0 / 3.0, 0.4936)])
+def test_xi0_matches_the_published_energy_constants(gamma, alpha):
+    # Sedov's energy integral alpha, tabulated for the spherical blast
+    # (Sedov, "Similarity and Dimensional Methods in Mechanics", 1959;
+    # Taylor, Proc. R. Soc. A 201, 1950, for gamma = 1.4), gives
+    # R = (E t^2 / (alpha rho0))^(1/5), i.e. xi0 = alpha^(-1/5).  The
+    # tabulated alpha carries 3-4 significant digits.
+    xi0 = S.profile(gamma)[4]
+    assert abs(xi0 / alpha ** -0.2 - 1.0) < 5e-4
