@@ -69,6 +69,8 @@ def workload(name):
         return C.concat_boxes(C.batch_boxes(64, seed=3))
     if name == "lognormal256":
         return C.lognormal(256, seed=5, sigma=4.0)
+    if name == "lognormal128":  # the same field law at 1/8 of the particles (profiling case)
+        return C.lognormal(128, seed=5, sigma=4.0)
     if name == "zeldovich256":
         return C.zeldovich(256, seed=5, amp=8.0)
     raise SystemExit(f"unknown workload {name}")

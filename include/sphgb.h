@@ -143,6 +143,8 @@ typedef struct sph_stats {
    * block sorts, 5 hierarchical merge, 6 interaction lists, 7 node h maxima */
   double build_ms[8];
   int32_t builds;            /* decompositions built while profiling (rebuilds included) */
+  int64_t sweep_gathered[8]; /* j entries the sweeps' axial windows held, per phase (before the
+                                chunk's box test; one per chunk, not per lane) */
 } sph_stats;
 
 /* Fill *p with the defaults listed above. */

@@ -891,10 +891,11 @@ int sph_profile(sph_ctx* c, int32_t enable) {
     c->prof_n[k] = 0;
     c->prof_units_acc[k] = 0;
     c->prof_cand_acc[k] = 0;
+    c->prof_gath_acc[k] = 0;
     c->prof_build_ms[k] = 0;
   }
   c->prof_builds = 0;
-  if (enable) SPH_TRY(dbuf_ensure(c->prof_units, 4096 * sizeof(unsigned long long)));
+  if (enable) SPH_TRY(dbuf_ensure(c->prof_units, 4 * 2048 * sizeof(unsigned long long)));
   c->profile = enable != 0;
   return SPH_OK;
 }
@@ -908,6 +909,7 @@ int sph_get_stats(sph_ctx* c, sph_stats* out) {
     st.sweep_launches[k] = c->prof_n[k];
     st.sweep_units[k] = (int64_t)c->prof_units_acc[k];
     st.sweep_candidates[k] = (int64_t)c->prof_cand_acc[k];
+    st.sweep_gathered[k] = (int64_t)c->prof_gath_acc[k];
   }
   for (int k = 0; k < 8; ++k) st.build_ms[k] = c->prof_build_ms[k];
   st.builds = c->prof_builds;

@@ -792,29 +792,36 @@ __device__ __forceinline__ float overlap1(float lo, float hi, float a, float b) 
   return w > 0.f ? fminf(fmaxf(o / w, 0.f), 1.f) : (lo >= a && lo <= b ? 1.f : 0.f);
 }
 
+// one warp per block: the lanes share the block's particles and its
+// interaction entries (heavy blocks hold thousands of entries), and the
+// partial sums meet in a fixed butterfly order
 __global__ void k_block_cost(int nblock, const int* b_first, const int* b_count,
                              const long long* dtoff, const int* dt_cj, const float4* dt_shift,
                              const float* h, const int* pflag, const int* ncount,
                              const float4* n_lo, const float4* n_hi, const float4* b_lo,
                              const float4* b_hi, const int* nseg, unsigned long long* cost,
                              unsigned long long* total, unsigned long long* maxc) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (b >= nblock) return;
   const int f = b_first[b], bn0 = b_count[b];
   float hm = 0.f;
   int bn = 0;  // particles to sweep (pflag: only those still iterating)
-  for (int k = 0; k < bn0; ++k) {
+  for (int k = lane; k < bn0; k += 32) {
     if (pflag && !(pflag[f + k] & 1)) continue;
     hm = fmaxf(hm, h[f + k]);
     ++bn;
   }
+  bn = __reduce_add_sync(0xffffffffu, bn);
   if (bn == 0) {
-    cost[b] = 0;
+    if (lane == 0) cost[b] = 0;
     return;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
   const float4 l0 = b_lo[b], h0 = b_hi[b];
-  double w = bn;
-  for (long long e = dtoff[b]; e < dtoff[b + 1]; ++e) {
+  double w = 0.0;
+  for (long long e = dtoff[b] + lane; e < dtoff[b + 1]; e += 32) {
     const int cj = dt_cj[e];
     const float4 sh = dt_shift[e];
     int nt;
@@ -833,7 +840,10 @@ __global__ void k_block_cost(int nblock, const int* b_first, const int* b_count,
                      overlap1(tl.z + sh.z, th.z + sh.z, l0.z - hm, h0.z + hm);
     w += (double)min(nt, 4096) * fr;
   }
-  w *= (double)((bn + 31) / 32);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  if (lane != 0) return;
+  w = (w + (double)bn) * (double)((bn + 31) / 32);
   const unsigned long long c = (unsigned long long)fmin(w, 4.0e9);
   cost[b] = c;
   atomicAdd(total, c);
@@ -1584,6 +1594,8 @@ static int make_plan(sph_ctx* c, const unsigned long long* bc, const unsigned lo
   SPH_TRY(d2h(&nunits, c->u_off.as<int>() + nblock, s));
   SPH_TRY(d2h(&npart, c->b_part.as<long long>() + nblock, s));
   c->nunits = nunits;
+  // active-unit list of masked sweeps: tile counts, the count, the units
+  SPH_TRY(dbuf_ensure(c->u_act, sizeof(int) * ((size_t)nunits + nunits / 1024 + 4)));
   SPH_TRY(dbuf_ensure(c->u_block, sizeof(int) * (nunits + 1)));
   SPH_TRY(dbuf_ensure(c->u_seg, sizeof(int) * (nunits + 1)));
   SPH_TRY(dbuf_ensure(c->u_e0, sizeof(long long) * (nunits + 1)));
@@ -1614,7 +1626,7 @@ static int estimate_costs(sph_ctx* c, const int* pflag, const float* h, const in
   unsigned long long* bc = c->b_cost.as<unsigned long long>() + (nblock + 1);
   unsigned long long* tot = c->plan_max.as<unsigned long long>();
   SPH_CUDA(cudaMemsetAsync(tot, 0, 2 * sizeof(unsigned long long), s));
-  { k_block_cost<<<div_up(nblock, TPB), TPB, 0, s>>>(
+  { k_block_cost<<<div_up((long long)nblock * 32, TPB), TPB, 0, s>>>(
       nblock, c->b_first.as<int>(), c->b_count.as<int>(), c->b_dtoff.as<long long>(),
       c->dt_cj.as<int>(), c->dt_shift.as<float4>(), h, pflag, c->n_count.as<int>(),
       c->n_lo.as<float4>(), c->n_hi.as<float4>(), c->b_lo.as<float4>(), c->b_hi.as<float4>(), nseg,

@@ -141,6 +141,7 @@ struct sph_ctx {
   int nunits = 0;
   DBuf b_nseg, u_off, b_part, u_block, u_seg, u_e0, u_e1, u_key, part, blk_done;
   DBuf plan_max;     // unsigned long long: largest estimated block cost of the last estimate
+  DBuf u_act;        // int: units of the active blocks in LPT order (masked sweeps)
   DBuf dt_cj;      // int
   DBuf dt_code;    // int: dir | (sgn+1) << 8
   DBuf dt_shift;   // float4 (sx, sy, sz, 0)
@@ -206,9 +207,10 @@ struct sph_ctx {
   struct Ev { int phase; cudaEvent_t a, b; };
   std::vector<Ev> ev_pending;
   std::vector<cudaEvent_t> ev_pool;
-  DBuf prof_units;  // unsigned long long per pending profiled launch
+  DBuf prof_units;  // 4 unsigned long long per pending profiled launch
   unsigned long long prof_units_acc[8] = {0};
   unsigned long long prof_cand_acc[8] = {0};
+  unsigned long long prof_gath_acc[8] = {0};
   double prof_ms[8] = {0};
   int prof_n[8] = {0};
   double prof_build_ms[8] = {0};

@@ -65,6 +65,7 @@ __device__ __forceinline__ unsigned make_tag(int j, float sx, float sy, float sz
 struct SweepArgs {
   int nblock;
   int nunits;           // work units (slices of the blocks' interaction lists)
+  const int* nunits_dev;  // non-null: the unit count of a compacted order, on the device
   int cap;  // buffered j-particles per warp between two compute passes
   const int* order;     // units in LPT order
   const int* u_block;   // unit -> block, slice index and entry range
@@ -120,7 +121,7 @@ struct SweepArgs {
   float4* o4;
   float4* o5;
   int* ocnt;
-  unsigned long long* units;  // profiling: accepted pairs of this launch
+  unsigned long long* units;  // profiling: accepted pairs, lane candidates, window entries
   // force pair lists (written by the force sweep, read by k_listeval)
   unsigned* fl_list;
   int* fl_cnt;
@@ -899,11 +900,12 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
   unsigned char* lst = reinterpret_cast<unsigned char*>(cpos + 32 + a.bmax / 4);
   const unsigned lt = (1u << lane) - 1u;
   if (a.run_if && *a.run_if == 0) return;
+  const int nun = a.nunits_dev ? *a.nunits_dev : a.nunits;
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(a.queue, 1);
     q = __shfl_sync(FULL, q, 0);
-    if (q >= a.nunits) break;
+    if (q >= nun) break;
     const int un = a.order[q];
     const int b = a.u_block[un];
     if (a.blk_active && a.blk_active[b] == 0) continue;
@@ -967,6 +969,7 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
 #pragma unroll
       for (int k = 0; k < P::NACC; ++k) acc[k] = cmp[k] = part[k] = 0.f;
       int cnt = 0, ncand = 0, staged = 0, wtot = 0;
+      long long ngath = 0;
       unsigned* wl = (P::WRITES && LIST && a.fl_list && vi && nseg == 1)
                          ? a.fl_list + ((size_t)(pi >> 5) * a.fl_K) * 32 + (pi & 31)
                          : nullptr;
@@ -1046,6 +1049,7 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
         }
         const int excl = incl - jn;
         const int total = __shfl_sync(FULL, incl, 31);
+        if (COUNT && a.units) ngath += total;
         // ---- flat gather over every window, filtered by the chunk's box
         for (int f0 = 0; f0 < total; f0 += 32) {
           const int f = f0 + lane;
@@ -1142,6 +1146,7 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
         if (lane == 0) {
           atomicAdd(a.units, (unsigned long long)ct);
           atomicAdd(a.units + 1, (unsigned long long)ncand);
+          atomicAdd(a.units + 2, (unsigned long long)ngath);
         }
       }
       __syncwarp();
@@ -1149,6 +1154,89 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
     }
     if (nseg > 1) combine_slices<P, COUNT, LIST>(a, b, bf, bn, nseg);
   }
+}
+
+// Masked sweeps (the h iteration's later rounds, the overflow sweeps after
+// the pair lists) touch few blocks; rather than have every warp claim and
+// skip hundreds of thousands of idle units through one atomic counter, the
+// units of the active blocks are compacted first, in LPT order: per tile of
+// UC_TILE units a count, then each tile adds the counts before it and
+// scatters its active units (a ballot scan per warp, the warps in order).
+constexpr int UC_TILE = 1024;
+constexpr int UC_THREADS = 256;
+
+__device__ __forceinline__ bool unit_on(const SweepArgs& a, int q) {
+  return a.blk_active[a.u_block[a.order[q]]] != 0;
+}
+
+__global__ void __launch_bounds__(UC_THREADS) k_unit_count(SweepArgs a, int* tcnt) {
+  int on = 0;
+  const bool run = !a.run_if || *a.run_if != 0;
+  for (int k = 0; k < UC_TILE / UC_THREADS; ++k) {
+    const int q = blockIdx.x * UC_TILE + k * UC_THREADS + threadIdx.x;
+    if (run && q < a.nunits) on += unit_on(a, q) ? 1 : 0;
+  }
+  on = __reduce_add_sync(FULL, on);
+  __shared__ int ws[UC_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = on;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < UC_THREADS / 32; ++w) t += ws[w];
+    tcnt[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(UC_THREADS) k_unit_compact(SweepArgs a, const int* tcnt,
+                                                            int ntiles, int* nact, int* out) {
+  __shared__ int ws[UC_THREADS / 32];
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int pre = 0;
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += UC_THREADS) pre += tcnt[t];
+  pre = __reduce_add_sync(FULL, pre);
+  if (lane == 0) ws[w] = pre;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = 0;
+    for (int k = 0; k < UC_THREADS / 32; ++k) b += ws[k];
+    base = b;
+  }
+  const bool run = !a.run_if || *a.run_if != 0;
+  for (int k = 0; k < UC_TILE / UC_THREADS; ++k) {
+    __syncthreads();  // base and ws are settled; ws may be overwritten
+    const int q = blockIdx.x * UC_TILE + k * UC_THREADS + threadIdx.x;
+    const bool on = run && q < a.nunits && unit_on(a, q);
+    const unsigned m = __ballot_sync(FULL, on);
+    if (lane == 0) ws[w] = __popc(m);
+    __syncthreads();
+    int off = base;
+    for (int v = 0; v < w; ++v) off += ws[v];
+    if (on) out[off + __popc(m & ((1u << lane) - 1u))] = a.order[q];
+    __syncthreads();  // every thread has read base and ws
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int v = 0; v < UC_THREADS / 32; ++v) t += ws[v];
+      base += t;
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == ntiles - 1 && threadIdx.x == 0) *nact = base;
+}
+
+// replaces the unit order of a masked sweep by the compacted one
+int compact_units(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
+  if (!a.blk_active || a.nunits == 0) return SPH_OK;
+  const int ntiles = div_up(a.nunits, UC_TILE);
+  int* tcnt = c->u_act.as<int>();
+  int* nact = tcnt + ntiles;
+  int* out = nact + 1;
+  { k_unit_count<<<ntiles, UC_THREADS, 0, s>>>(a, tcnt); note_launch(); }
+  { k_unit_compact<<<ntiles, UC_THREADS, 0, s>>>(a, tcnt, ntiles, nact, out); note_launch(); }
+  SPH_CUDA(cudaGetLastError());
+  a.order = out;
+  a.nunits_dev = nact;
+  return SPH_OK;
 }
 
 template <class P, bool COUNT, bool LIST>
@@ -1170,12 +1258,13 @@ int launch_shape(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
   if (grid > maxgrid) grid = maxgrid > 0 ? maxgrid : 1;
   c->sweep_grid = grid;
   c->sweep_threads = 32 * warps;
+  SPH_TRY(compact_units(c, a, s));
   SPH_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), s));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile) {
     if (c->ev_pending.size() >= 2048) SPH_TRY(prof_resolve(c));
-    a.units = c->prof_units.as<unsigned long long>() + 2 * c->ev_pending.size();
-    SPH_CUDA(cudaMemsetAsync(a.units, 0, 2 * sizeof(unsigned long long), s));
+    a.units = c->prof_units.as<unsigned long long>() + 4 * c->ev_pending.size();
+    SPH_CUDA(cudaMemsetAsync(a.units, 0, 4 * sizeof(unsigned long long), s));
     e0 = ev_get(c);
     e1 = ev_get(c);
     SPH_CUDA(cudaEventRecord(e0, s));
@@ -1283,8 +1372,8 @@ int launch_listeval(sph_ctx* c, SweepArgs& a, cudaStream_t s) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profile) {
     if (c->ev_pending.size() >= 2048) SPH_TRY(prof_resolve(c));
-    a.units = c->prof_units.as<unsigned long long>() + 2 * c->ev_pending.size();
-    SPH_CUDA(cudaMemsetAsync(a.units, 0, 2 * sizeof(unsigned long long), s));
+    a.units = c->prof_units.as<unsigned long long>() + 4 * c->ev_pending.size();
+    SPH_CUDA(cudaMemsetAsync(a.units, 0, 4 * sizeof(unsigned long long), s));
     e0 = ev_get(c);
     e1 = ev_get(c);
     SPH_CUDA(cudaEventRecord(e0, s));
@@ -1348,7 +1437,7 @@ cudaEvent_t ev_get(sph_ctx* c) {
 }
 
 int prof_resolve(sph_ctx* c) {
-  std::vector<unsigned long long> units(2 * c->ev_pending.size());
+  std::vector<unsigned long long> units(4 * c->ev_pending.size());
   if (!units.empty())
     SPH_CUDA(cudaMemcpy(units.data(), c->prof_units.p, units.size() * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost));
@@ -1360,8 +1449,9 @@ int prof_resolve(sph_ctx* c) {
     if (e.phase >= 0 && e.phase < 8) {
       c->prof_ms[e.phase] += ms;
       c->prof_n[e.phase] += 1;
-      c->prof_units_acc[e.phase] += units[2 * k];
-      c->prof_cand_acc[e.phase] += units[2 * k + 1];
+      c->prof_units_acc[e.phase] += units[4 * k];
+      c->prof_cand_acc[e.phase] += units[4 * k + 1];
+      c->prof_gath_acc[e.phase] += units[4 * k + 2];
     }
     ++k;
     c->ev_pool.push_back(e.a);

@@ -222,6 +222,7 @@ class SPH:
         d["sweep_launches"] = list(st.sweep_launches)
         d["sweep_units"] = list(st.sweep_units)
         d["sweep_candidates"] = list(st.sweep_candidates)
+        d["sweep_gathered"] = list(st.sweep_gathered)
         d["newton_active"] = list(st.newton_active)
         return d
 

@@ -1,9 +1,12 @@
 """GPU parity of the force with the Monaghan-Balsara viscosity and of the
 time step of Eq. (dt) (Section 4.1) against the FP64 oracle, through the
 C ABI (sph_force_viscous).  Tolerances as for the inviscid force: 1e-4 of
-the rms for accelerations and du/dt; the switch and the time step (a
-maximum over pairs, which can change where the FP32 and FP64 neighbour
-tests straddle r = h) per particle at the 99.9th percentile."""
+the rms for accelerations and du/dt, and 1e-4 on every element of the
+Balsara switch (continuous in r at r = h, since the kernel's slope vanishes
+there).  The time step is a maximum over pairs, which jumps where a pair
+straddles r = max(h_i, h_j) between the FP32 and FP64 neighbour tests:
+every particle with no pair within 3e-5 of that radius (30x the h parity)
+matches to 1e-4, and the few that have one are counted and bounded."""
 import numpy as np
 import pytest
 import torch
@@ -23,6 +26,22 @@ def _built():
 
 def _t(a):
     return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _straddlers(x, h, eps=3e-5):
+    """Particles with a pair at r / max(h_i, h_j) within eps of 1 (periodic
+    unit box), found by a KD-tree query independent of both codes."""
+    from scipy.spatial import cKDTree
+    t = cKDTree(np.mod(x, 1.0), boxsize=1.0)
+    P = t.query_pairs(h.max() * (1 + eps), output_type="ndarray")
+    d = x[P[:, 0]] - x[P[:, 1]]
+    d -= np.round(d)
+    q = np.linalg.norm(d, axis=1) / np.maximum(h[P[:, 0]], h[P[:, 1]])
+    near = np.abs(q - 1.0) < eps
+    out = np.zeros(len(x), dtype=bool)
+    out[P[near, 0]] = True
+    out[P[near, 1]] = True
+    return out
 
 
 def _rms_err(a, ref):
@@ -53,9 +72,12 @@ def test_viscous_force_switch_and_time_step_match_the_oracle(case):
     assert _rms_err(a, a_ref) <= 1e-4
     assert np.max(np.abs(du - du_ref)) / np.sqrt(np.mean(du_ref ** 2)) <= 1e-4
     fe = np.abs(f.cpu().numpy().astype(np.float64) - vis["balsara"])
-    assert np.quantile(fe, 0.999) <= 1e-4 and fe.max() <= 1e-2
+    assert fe.max() <= 1e-4, (fe.max(), int((fe > 1e-4).sum()))
     te = np.abs(dt.cpu().numpy().astype(np.float64) / vis["dt"] - 1.0)
-    assert np.quantile(te, 0.999) <= 1e-4 and te.max() <= 5e-2
+    st = _straddlers(d["x"], ref["h"])
+    assert te[~st].max() <= 1e-4, (te[~st].max(), int((te[~st] > 1e-4).sum()))
+    assert st.sum() <= 0.02 * len(st) and int((te > 1e-4).sum()) <= st.sum()
+    assert te.max() <= 5e-2
     # exact conservation of the pairwise terms, to FP32 summation
     m = d["m"].astype(np.float64)
     ma = m[:, None] * a
@@ -75,7 +97,7 @@ def test_zero_viscosity_is_the_inviscid_force(case):
     assert np.max(np.abs(d0 - d1)) <= 1e-6 * np.sqrt(np.mean(d1 ** 2))
     # the time step does not depend on alpha
     te = np.abs(dt0.cpu().numpy().astype(np.float64) / vis["dt"] - 1.0)
-    assert np.quantile(te, 0.999) <= 1e-4
+    assert te[~_straddlers(d["x"], ref["h"])].max() <= 1e-4
 
 
 def test_viscous_force_needs_a_density_and_velocities():
