@@ -145,6 +145,9 @@ typedef struct sph_stats {
   int32_t builds;            /* decompositions built while profiling (rebuilds included) */
   int64_t sweep_gathered[8]; /* j entries the sweeps' axial windows held, per phase (before the
                                 chunk's box test; one per chunk, not per lane) */
+  int32_t pairs_unlisted;    /* particles the last force sweep recorded no pair list for (swept
+                                again by the phases over the force pairs) ... */
+  int32_t pairs_unlisted_cut; /* ... of which in blocks cut into several work units */
 } sph_stats;
 
 /* Fill *p with the defaults listed above. */

@@ -43,6 +43,7 @@ class SphStats(C.Structure):
         ("sweep_launches", C.c_int32 * 8), ("sweep_units", C.c_int64 * 8), ("sweep_candidates", C.c_int64 * 8),
         ("newton_active", C.c_int32 * 32), ("unconverged", C.c_int32), ("sweep_grid", C.c_int32), ("sweep_threads", C.c_int32),
         ("build_ms", C.c_double * 8), ("builds", C.c_int32), ("sweep_gathered", C.c_int64 * 8),
+        ("pairs_unlisted", C.c_int32), ("pairs_unlisted_cut", C.c_int32),
     ]
 
 

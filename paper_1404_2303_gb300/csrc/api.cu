@@ -549,7 +549,8 @@ void sph_destroy(sph_ctx* c) {
                  &c->fl_over, &c->task_ctl, &c->tree_ctl, &c->visc4, &c->dt_s,
                  &c->b_nseg, &c->u_off, &c->b_part, &c->u_block, &c->u_seg, &c->u_e0, &c->u_e1,
                  &c->u_key, &c->part, &c->blk_done, &c->vv_acc, &c->vv_du, &c->vv_dt,
-                 &c->vv_vp, &c->vv_up, &c->vv_h, &c->vv_tmp, &c->vv_red};
+                 &c->vv_vp, &c->vv_up, &c->vv_h, &c->vv_tmp, &c->vv_red, &c->plan_max,
+                 &c->u_act, &c->sl_list};
   for (DBuf* b : all) dbuf_free(*b);
   for (auto& e : c->ev_pending) {
     cudaEventDestroy(e.a);
@@ -932,6 +933,15 @@ int sph_get_stats(sph_ctx* c, sph_stats* out) {
   st.max_depth = c->max_depth;
   for (int b = 0; b < 8; ++b) st.top_level[b] = b < c->nbox ? c->box_t[b] : 0;
   st.sorted_entries = c->sorted_entries;
+  st.pairs_unlisted = 0;
+  st.pairs_unlisted_cut = 0;
+  if (c->fl_valid && c->fl_over.p) {
+    int ov[2] = {0, 0};
+    SPH_CUDA(cudaDeviceSynchronize());
+    SPH_CUDA(cudaMemcpy(ov, c->fl_over.p, sizeof(ov), cudaMemcpyDeviceToHost));
+    st.pairs_unlisted = ov[0];
+    st.pairs_unlisted_cut = ov[1];
+  }
   *out = st;
   return SPH_OK;
 }

@@ -1049,6 +1049,9 @@ __global__ void k_gather_i64(int n, const int* idx, const long long* in, long lo
 constexpr int MS_CAP = LIST_CAP;
 constexpr int MS_SUB = LIST_SUB;
 constexpr int MS_TPB = 256;
+constexpr int MW_CAP = 512;    // largest segment merged by one warp (k_merge_warp)
+constexpr int MW_WARPS = 8;
+constexpr long long MW_MIN_SEGS = 65536;  // segments in a generation before small ones go to warps
 
 __global__ void k_merge_count(int g0, int g1, const int* need, const int* child0, const int* nblk,
                               const int* count, const int* listed, long long* segs) {
@@ -1080,6 +1083,77 @@ __device__ __forceinline__ int count_less_s(const float* k, const int* ix, int n
   return lo;
 }
 
+// Small segments (most of them: a leaf's few blocks, a cell of a few
+// hundred particles) leave a 256-thread CTA mostly idle; there one warp
+// merges one segment, MW_WARPS segments per CTA, with the same ranking:
+// each element's merged position is its index in its own sub-list plus its
+// rank (binary search) in every other sub-list.
+__global__ void __launch_bounds__(MW_WARPS * 32)
+    k_merge_warp(long long seg0, long long nseg, const int* seg_node, const unsigned char* seg_dir,
+                 const int* child0, const int* count, const int* nblk, const int* blk0,
+                 const int* b_first, const int* b_count, const long long* sbase, float* s_key,
+                 int* s_idx) {
+  __shared__ float Ks[MW_WARPS][MW_CAP];
+  __shared__ int Xs[MW_WARPS][MW_CAP];
+  __shared__ int sos[MW_WARPS][MS_SUB + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long sg = seg0 + (long long)blockIdx.x * MW_WARPS + w;
+  if (sg >= seg0 + nseg) return;
+  const int node = seg_node[sg];
+  if (count[node] > MW_CAP) return;  // merged by k_merge_smem (the launch passes small_cap)
+  const int d = seg_dir[sg];
+  float* K = Ks[w];
+  int* X = Xs[w];
+  int* so = sos[w];
+  const bool leaf = child0[node] < 0;
+  const int nsub = leaf ? nblk[node] : 8;
+  int sc = 0;
+  long long base = 0;
+  if (lane < nsub) {
+    if (leaf) {
+      const int bi = blk0[node] + lane;
+      sc = b_count[bi];
+      base = 13ll * b_first[bi] + (long long)d * sc;
+    } else {
+      const int ch = child0[node] + lane;
+      sc = count[ch];
+      base = sc > 0 ? sbase[ch] + (long long)d * sc : 0;
+    }
+  }
+  int incl = sc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane < nsub) so[lane] = incl - sc;
+  if (lane == nsub - 1) so[nsub] = incl;
+  const long long dst0 = sbase[node] + (long long)d * count[node];
+  for (int q = 0; q < nsub; ++q) {
+    const int o = __shfl_sync(0xffffffffu, incl - sc, q), c = __shfl_sync(0xffffffffu, sc, q);
+    const long long b = __shfl_sync(0xffffffffu, base, q);
+    for (int e = lane; e < c; e += 32) {
+      K[o + e] = s_key[b + e];
+      X[o + e] = s_idx[b + e];
+    }
+  }
+  __syncwarp();
+  const int total = so[nsub];
+  for (int e = lane; e < total; e += 32) {
+    int q = 0;
+    while (e >= so[q + 1]) ++q;
+    const float kv = K[e];
+    const int iv = X[e];
+    int rank = e - so[q];
+    for (int o = 0; o < nsub; ++o) {
+      if (o == q) continue;
+      rank += count_less_s(K + so[o], X + so[o], so[o + 1] - so[o], kv, iv);
+    }
+    s_key[dst0 + rank] = kv;
+    s_idx[dst0 + rank] = iv;
+  }
+}
+
 // one CTA per (node, direction) segment: the sub-lists (children's or the
 // leaf's blocks' lists of that direction) are loaded side by side into
 // shared memory and every element is ranked against the other sub-lists
@@ -1087,13 +1161,18 @@ __global__ void __launch_bounds__(MS_TPB)
     k_merge_smem(long long seg0, const int* seg_node, const unsigned char* seg_dir,
                  const int* child0, const int* count, const int* nblk, const int* blk0,
                  const int* b_first, const int* b_count, const long long* sbase, float* s_key,
-                 int* s_idx) {
+                 int* s_idx, int small_cap) {
   __shared__ float K[MS_CAP];
   __shared__ int X[MS_CAP];
   __shared__ int so[MS_SUB + 1];
   __shared__ long long sb[MS_SUB];
   __shared__ long long dst0;
   __shared__ int nsub_s;
+  {
+    // segments of at most small_cap elements are merged by k_merge_warp
+    const int node = seg_node[seg0 + blockIdx.x];
+    if (count[node] <= small_cap) return;
+  }
   if (threadIdx.x < 32) {
     // the first warp reads the sub-lists' sizes and bases in parallel and
     // scans them into offsets
@@ -1603,6 +1682,7 @@ static int make_plan(sph_ctx* c, const unsigned long long* bc, const unsigned lo
   SPH_TRY(dbuf_ensure(c->u_key, sizeof(unsigned long long) * (nunits + 1) * 2));
   SPH_TRY(dbuf_ensure(c->b_order, sizeof(int) * (nunits + 1) * 2));
   SPH_TRY(dbuf_ensure(c->part, sizeof(float) * (size_t)(npart + 1)));
+  c->part_cols = npart / SPH_PART_STRIDE;
   SPH_TRY(dbuf_ensure(c->blk_done, sizeof(int) * (nblock + 1)));
   SPH_CUDA(cudaMemsetAsync(c->blk_done.p, 0, sizeof(int) * (nblock + 1), s));
   unsigned long long* uk = c->u_key.as<unsigned long long>();
@@ -1778,10 +1858,21 @@ static int build_blocks_and_sorts(sph_ctx* c, cudaStream_t s) {
       const int g0 = c->gen_start[g], g1 = c->gen_start[g + 1];
       const long long nseg = goff[g + 1] - goff[g];
       if (g1 <= g0 || nseg <= 0) continue;
+      // a generation with many segments merges its small ones one warp
+      // each (more segments in flight per SM); a generation with few keeps
+      // 256 threads per segment (more parallelism per segment)
+      const int small_cap = nseg >= MW_MIN_SEGS ? MW_CAP : 0;
+      if (small_cap > 0) {
+        k_merge_warp<<<(unsigned)div_up(nseg, MW_WARPS), MW_WARPS * 32, 0, s>>>(
+            goff[g], nseg, seg_node, seg_dir, c->n_child0.as<int>(), c->n_count.as<int>(), nblk,
+            blk0, c->b_first.as<int>(), c->b_count.as<int>(), c->n_sbase.as<long long>(),
+            c->s_key.as<float>(), c->s_idx.as<int>());
+        note_launch();
+      }
       { k_merge_smem<<<(unsigned)nseg, MS_TPB, 0, s>>>(
           goff[g], seg_node, seg_dir, c->n_child0.as<int>(), c->n_count.as<int>(), nblk, blk0,
           c->b_first.as<int>(), c->b_count.as<int>(), c->n_sbase.as<long long>(),
-          c->s_key.as<float>(), c->s_idx.as<int>()); note_launch(); }
+          c->s_key.as<float>(), c->s_idx.as<int>(), small_cap); note_launch(); }
       SPH_CUDA(cudaGetLastError());
     }
     SPH_CUDA(cudaStreamSynchronize(s));  // the table is freed below

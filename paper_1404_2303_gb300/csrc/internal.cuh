@@ -140,6 +140,8 @@ struct sph_ctx {
   // units in LPT order); partial sums of blocks cut into several units
   int nunits = 0;
   DBuf b_nseg, u_off, b_part, u_block, u_seg, u_e0, u_e1, u_key, part, blk_done;
+  long long part_cols = 0;  // (slice, particle) columns of the blocks cut into slices
+  DBuf sl_list;             // unsigned: the slices' pair lists, pair_list_cap per column
   DBuf plan_max;     // unsigned long long: largest estimated block cost of the last estimate
   DBuf u_act;        // int: units of the active blocks in LPT order (masked sweeps)
   DBuf dt_cj;      // int

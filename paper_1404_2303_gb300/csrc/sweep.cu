@@ -84,6 +84,7 @@ struct SweepArgs {
   const float4* dt_shift;
   const int* n_count;
   const long long* n_sbase;
+  const int* n_child0;  // first child of a cell (-1: leaf)
   const float* n_hmax;
   const float* b_hmax;
   const float4* n_lo;   // particle bounding boxes of cells and blocks
@@ -124,6 +125,7 @@ struct SweepArgs {
   unsigned long long* units;  // profiling: accepted pairs, lane candidates, window entries
   // force pair lists (written by the force sweep, read by k_listeval)
   unsigned* fl_list;
+  unsigned* sl_list;    // pair lists of the slices of blocks cut into work units
   int* fl_cnt;
   int* fl_flag;
   int* fl_blk;
@@ -149,7 +151,7 @@ struct SweepArgs {
 // ---------------------------------------------------------------------------
 struct PDensity {
   static constexpr int NACC = 5;
-  static constexpr int MINB = 3;  // resident CTAs per SM the register budget is set for
+  static constexpr int MINB = 4;  // resident CTAs per SM the register budget is set for
   static constexpr int NMAX = 0;  // trailing accumulators that take a maximum
   static constexpr int JW = 1;
   static constexpr bool WRITES = false;
@@ -830,14 +832,27 @@ __device__ __forceinline__ void compute_pass(const typename P::I& I, bool vi, co
     (out) = lo_;                                 \
   } while (0)
 
-// factor-2 band of a particle's h above the block's smallest h (0..15);
-// 31 for particles that need no sweep (converged during the h iteration, or
-// with a recorded pair list in a masked sweep)
+// a listed target of at least DESC_MIN particles of which the chunk's reach
+// covers less than DESC_FRAC of the box is swept through its children
+constexpr int DESC_MIN = 64;
+constexpr float DESC_FRAC = 0.5f;
+
+// fraction of [lo, hi] inside [a, b] (a point: 1 inside, 0 outside)
+__device__ __forceinline__ float overlap_frac(float lo, float hi, float a, float b) {
+  const float w = hi - lo;
+  const float o = fminf(hi, b) - fmaxf(lo, a);
+  return w > 0.f ? fminf(fmaxf(o / w, 0.f), 1.f) : (lo >= a && lo <= b ? 1.f : 0.f);
+}
+
+// band of a particle's h above the block's smallest h, HCLASS bands per
+// factor 2 (0..15 HCLASS); 31 for particles that need no sweep (converged
+// during the h iteration, or with a recorded pair list in a masked sweep)
+constexpr int HCLASS = 1;
 __device__ __forceinline__ int h_class(const SweepArgs& a, int p, float hmin) {
   if (a.pflag && !(a.pflag[p] & 1)) return 31;
   const float r = a.h[p] / hmin;
-  const int c = r < 2.f ? 0 : (int)__log2f(r);
-  return c > 15 ? 15 : c;
+  const int c = r < 1.f ? 0 : (int)((float)HCLASS * __log2f(r));
+  return c > 15 * HCLASS ? 15 * HCLASS : c;
 }
 
 // shared memory of one warp, in float4: j buffer, chunk positions, the
@@ -878,11 +893,39 @@ __device__ __noinline__ void combine_slices(const SweepArgs& a, int b, int bf, i
     }
     P::finalize(a, p, v);
     if (COUNT && a.ocnt) a.ocnt[p] = cg;
-    if (P::WRITES && LIST && a.fl_list) {  // no list for a sliced block: swept later
-      a.fl_cnt[p] = -1;
-      a.fl_flag[p] = 1;
-      atomicAdd(a.fl_over, 1);
-      a.fl_blk[b] = 1;
+    if (P::WRITES && LIST && a.fl_list) {
+      // the particle's list: its slices' lists in slice order, unless one
+      // of them overflowed or they do not fit together (then it is swept
+      // by the phases that follow)
+      static_assert(!P::WRITES || P::NACC + 2 <= SPH_PART_STRIDE, "slice list count slot");
+      int tot = 0;
+      bool ok = a.sl_list != nullptr;
+      for (int sg = 0; sg < nseg && ok; ++sg) {
+        const int ci = __float_as_int(
+            __ldcg(a.part + a.b_part[b] + ((size_t)sg * bn + k) * SPH_PART_STRIDE + P::NACC + 1));
+        ok = ci >= 0;
+        tot += ci;
+      }
+      ok = ok && tot <= a.fl_K;
+      if (ok) {
+        unsigned* dst = a.fl_list + ((size_t)(p >> 5) * a.fl_K) * 32 + (p & 31);
+        int e = 0;
+        for (int sg = 0; sg < nseg; ++sg) {
+          const long long col = a.b_part[b] / SPH_PART_STRIDE + (long long)sg * bn + k;
+          const unsigned* src = a.sl_list + ((size_t)(col >> 5) * a.fl_K) * 32 + (col & 31);
+          const int ci = __float_as_int(
+              __ldcg(a.part + a.b_part[b] + ((size_t)sg * bn + k) * SPH_PART_STRIDE + P::NACC + 1));
+          for (int q = 0; q < ci; ++q, ++e) dst[(size_t)e * 32] = __ldcg(src + (size_t)q * 32);
+        }
+        a.fl_cnt[p] = tot;
+        a.fl_flag[p] = 0;
+      } else {
+        a.fl_cnt[p] = -1;
+        a.fl_flag[p] = 1;
+        atomicAdd(a.fl_over, 1);
+        atomicAdd(a.fl_over + 1, 1);
+        a.fl_blk[b] = 1;
+      }
     }
   }
   __syncwarp();
@@ -970,49 +1013,23 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
       for (int k = 0; k < P::NACC; ++k) acc[k] = cmp[k] = part[k] = 0.f;
       int cnt = 0, ncand = 0, staged = 0, wtot = 0;
       long long ngath = 0;
-      unsigned* wl = (P::WRITES && LIST && a.fl_list && vi && nseg == 1)
-                         ? a.fl_list + ((size_t)(pi >> 5) * a.fl_K) * 32 + (pi & 31)
-                         : nullptr;
-      for (long long g = e0; g < e1; g += 32) {
-        // ---- one lane per interaction task: window of the chunk in the
-        // task cell's sorted list (the axial cutoff of the sorted sweep)
-        const long long e = g + lane;
-        const bool ve = e < e1;
-        int cj = 0, code = 1 << 8, ncj = 0;
-        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
-        long long jb = 0;
-        float hj = 0.f;
-        if (ve) {
-          cj = a.dt_cj[e];
-          code = a.dt_code[e];
-          sh = a.dt_shift[e];
-          float4 tlo, thi;
-          if (cj >= 0) {  // a cell with sorted lists
-            ncj = a.n_count[cj];
-            jb = a.n_sbase[cj];
-            if (P::USES_HJ) hj = a.n_hmax[cj];
-            tlo = a.n_lo[cj];
-            thi = a.n_hi[cj];
-          } else {        // a block of a cell without them
-            const int bj = -1 - cj;
-            ncj = a.b_count[bj];
-            jb = 13ll * a.b_first[bj];
-            if (P::USES_HJ) hj = a.b_hmax[bj];
-            tlo = a.b_lo[bj];
-            thi = a.b_hi[bj];
-          }
-          // a target whose box lies beyond the reach of the whole chunk has
-          // no candidate (the margin delta covers the rounding of the shift)
-          const float gx = fmaxf(fmaxf(__fadd_rn(tlo.x, sh.x) - bx1, bx0 - __fadd_rn(thi.x, sh.x)), 0.f);
-          const float gy = fmaxf(fmaxf(__fadd_rn(tlo.y, sh.y) - by1, by0 - __fadd_rn(thi.y, sh.y)), 0.f);
-          const float gz = fmaxf(fmaxf(__fadd_rn(tlo.z, sh.z) - bz1, bz0 - __fadd_rn(thi.z, sh.z)), 0.f);
-          const float Ct = (P::USES_HJ ? fmaxf(hmx, hj) : hmx) + a.delta;
-          if (!a.naive && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) > Ct * Ct) ncj = 0;
+      // pair-list column: the particle's own, or for a block cut into
+      // slices this slice's column (the last slice concatenates them)
+      unsigned* wl = nullptr;
+      if (P::WRITES && LIST && a.fl_list && vi) {
+        if (nseg == 1) {
+          wl = a.fl_list + ((size_t)(pi >> 5) * a.fl_K) * 32 + (pi & 31);
+        } else if (a.sl_list) {
+          const long long col = a.b_part[b] / SPH_PART_STRIDE + (long long)seg * bn + (pi - bf);
+          wl = a.sl_list + ((size_t)(col >> 5) * a.fl_K) * 32 + (col & 31);
         }
-        const int dir = code & 255, sgn = (code >> 8) - 1;
-        jb += (long long)dir * ncj;
+      }
+      // window of the chunk in one target's sorted list of direction dir
+      // (the axial cutoff of the sorted sweep): [js, js + jn) of its ncj
+      // entries; hj is the target's largest h (phases over max(h_i, h_j))
+      auto window = [&](const float* K, int ncj, int dir, int sgn, float ksh, float hj, int& js,
+                        int& jn) {
         const float ux = c_dir[dir][0], uy = c_dir[dir][1], uz = c_dir[dir][2];
-        const float ksh = sgn != 0 ? sort_key(sh.x, sh.y, sh.z, ux, uy, uz) : 0.f;
         float U = -FLT_MAX, L = FLT_MAX;
         for (int p = 0; p < nc; ++p) {
           const float4 c = cpos[p];
@@ -1022,25 +1039,25 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
           U = fmaxf(U, sk + ct);
           L = fminf(L, k - ct);
         }
-        int js = 0, jn = 0;
-        if (a.naive) {
-          jn = ve ? ncj : 0;  // every particle of the target is a candidate
-        } else if (ve && ncj > 0) {
-          const float* K = a.s_key + jb;
-          if (sgn > 0) {
-            SPH_PARTITION(ncj, K[mid] + ksh <= U, jn);
-          } else if (sgn < 0) {
-            SPH_PARTITION(ncj, -(K[mid] + ksh) > U, js);
-            jn = ncj - js;
-          } else {
-            int je;
-            SPH_PARTITION(ncj, K[mid] < L, js);
-            SPH_PARTITION(ncj, K[mid] <= U, je);
-            jn = max(je - js, 0);
-          }
+        js = 0;
+        jn = 0;
+        if (ncj <= 0) return;
+        if (sgn > 0) {
+          SPH_PARTITION(ncj, K[mid] + ksh <= U, jn);
+        } else if (sgn < 0) {
+          SPH_PARTITION(ncj, -(K[mid] + ksh) > U, js);
+          jn = ncj - js;
+        } else {
+          int je;
+          SPH_PARTITION(ncj, K[mid] < L, js);
+          SPH_PARTITION(ncj, K[mid] <= U, je);
+          jn = max(je - js, 0);
         }
-        const float C = (P::USES_HJ ? fmaxf(hmx, hj) : hmx) + a.delta;
-        const float C2 = C * C;
+      };
+      // flat gather over the 32 lanes' windows (lane l: entries [js, js + jn)
+      // of the list at jb, shifted by sh), filtered by the chunk's box, into
+      // the shared buffer (a compute pass whenever it fills)
+      auto gather = [&](long long jb, int js, int jn, float4 sh, float C2) {
         int incl = jn;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1050,7 +1067,6 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
         const int excl = incl - jn;
         const int total = __shfl_sync(FULL, incl, 31);
         if (COUNT && a.units) ngath += total;
-        // ---- flat gather over every window, filtered by the chunk's box
         for (int f0 = 0; f0 < total; f0 += 32) {
           const int f = f0 + lane;
           int k = 0;
@@ -1097,6 +1113,100 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
                      staged + __popc(mt & lt), cap);
           staged += nt;
         }
+      };
+      // fraction of a target box (shifted) inside the chunk's box grown by C
+      auto reach_frac = [&](float4 tlo, float4 thi, float4 sh, float C) {
+        return overlap_frac(__fadd_rn(tlo.x, sh.x), __fadd_rn(thi.x, sh.x), bx0 - C, bx1 + C) *
+               overlap_frac(__fadd_rn(tlo.y, sh.y), __fadd_rn(thi.y, sh.y), by0 - C, by1 + C) *
+               overlap_frac(__fadd_rn(tlo.z, sh.z), __fadd_rn(thi.z, sh.z), bz0 - C, bz1 + C);
+      };
+      for (long long g = e0; g < e1; g += 32) {
+        // ---- one lane per interaction task
+        const long long e = g + lane;
+        const bool ve = e < e1;
+        int cj = 0, code = 1 << 8, ncj = 0;
+        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+        long long jb = 0;
+        float hj = 0.f;
+        bool desc = false;
+        if (ve) {
+          cj = a.dt_cj[e];
+          code = a.dt_code[e];
+          sh = a.dt_shift[e];
+          float4 tlo, thi;
+          if (cj >= 0) {  // a cell with sorted lists
+            ncj = a.n_count[cj];
+            jb = a.n_sbase[cj];
+            if (P::USES_HJ) hj = a.n_hmax[cj];
+            tlo = a.n_lo[cj];
+            thi = a.n_hi[cj];
+          } else {        // a block of a cell without them
+            const int bj = -1 - cj;
+            ncj = a.b_count[bj];
+            jb = 13ll * a.b_first[bj];
+            if (P::USES_HJ) hj = a.b_hmax[bj];
+            tlo = a.b_lo[bj];
+            thi = a.b_hi[bj];
+          }
+          // a target whose box lies beyond the reach of the whole chunk has
+          // no candidate (the margin delta covers the rounding of the shift)
+          const float gx = fmaxf(fmaxf(__fadd_rn(tlo.x, sh.x) - bx1, bx0 - __fadd_rn(thi.x, sh.x)), 0.f);
+          const float gy = fmaxf(fmaxf(__fadd_rn(tlo.y, sh.y) - by1, by0 - __fadd_rn(thi.y, sh.y)), 0.f);
+          const float gz = fmaxf(fmaxf(__fadd_rn(tlo.z, sh.z) - bz1, bz0 - __fadd_rn(thi.z, sh.z)), 0.f);
+          const float Ct = (P::USES_HJ ? fmaxf(hmx, hj) : hmx) + a.delta;
+          if (!a.naive && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) > Ct * Ct) ncj = 0;
+          // in a phase over r < max(h_i, h_j), a large target of which the
+          // chunk reaches a small part is swept through its children's lists
+          // (each with its own box and largest h, where the target's largest
+          // h would widen every window), which prunes the far children and
+          // narrows the windows
+          desc = P::USES_HJ && !a.naive && cj >= 0 && ncj >= DESC_MIN && a.n_child0[cj] >= 0 &&
+                 reach_frac(tlo, thi, sh, Ct) < DESC_FRAC;
+        }
+        const int dir = code & 255, sgn = (code >> 8) - 1;
+        jb += (long long)dir * ncj;
+        const float ksh = sgn != 0 ? sort_key(sh.x, sh.y, sh.z, c_dir[dir][0], c_dir[dir][1],
+                                              c_dir[dir][2])
+                                   : 0.f;
+        int js = 0, jn = 0;
+        if (a.naive) {
+          jn = ve ? ncj : 0;  // every particle of the target is a candidate
+        } else if (ve && !desc) {
+          window(a.s_key + jb, ncj, dir, sgn, ksh, hj, js, jn);
+        }
+        const float C = (P::USES_HJ ? fmaxf(hmx, hj) : hmx) + a.delta;
+        gather(jb, js, jn, sh, C * C);
+        // ---- the descended targets, one at a time: lane l < 8 takes child l
+        unsigned dm = __ballot_sync(FULL, desc);
+        while (dm) {
+          const int t = __ffs(dm) - 1;
+          dm &= dm - 1;
+          const int cjt = __shfl_sync(FULL, cj, t), codet = __shfl_sync(FULL, code, t);
+          const float4 sht = make_float4(__shfl_sync(FULL, sh.x, t), __shfl_sync(FULL, sh.y, t),
+                                         __shfl_sync(FULL, sh.z, t), 0.f);
+          const float kst = __shfl_sync(FULL, ksh, t);
+          const int dirt = codet & 255, sgnt = (codet >> 8) - 1;
+          int nch = 0, jsc = 0, jnc = 0;
+          long long jbc = 0;
+          float hjc = 0.f;
+          if (lane < 8) {
+            const int ch = a.n_child0[cjt] + lane;
+            nch = a.n_count[ch];
+            if (nch > 0) {
+              if (P::USES_HJ) hjc = a.n_hmax[ch];
+              const float4 clo = a.n_lo[ch], chi = a.n_hi[ch];
+              const float Cc = (P::USES_HJ ? fmaxf(hmx, hjc) : hmx) + a.delta;
+              const float gx = fmaxf(fmaxf(__fadd_rn(clo.x, sht.x) - bx1, bx0 - __fadd_rn(chi.x, sht.x)), 0.f);
+              const float gy = fmaxf(fmaxf(__fadd_rn(clo.y, sht.y) - by1, by0 - __fadd_rn(chi.y, sht.y)), 0.f);
+              const float gz = fmaxf(fmaxf(__fadd_rn(clo.z, sht.z) - bz1, bz0 - __fadd_rn(chi.z, sht.z)), 0.f);
+              if (fmaf(gz, gz, fmaf(gy, gy, gx * gx)) > Cc * Cc) nch = 0;  // beyond reach
+              jbc = a.n_sbase[ch] + (long long)dirt * a.n_count[ch];
+            }
+          }
+          if (nch > 0) window(a.s_key + jbc, nch, dirt, sgnt, kst, hjc, jsc, jnc);
+          const float Cc = (P::USES_HJ ? fmaxf(hmx, hjc) : hmx) + a.delta;
+          gather(jbc, jsc, jnc, sht, Cc * Cc);
+        }
       }
       compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot, a.fl_K, sub,
                                    G);
@@ -1122,6 +1232,7 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
 #pragma unroll
           for (int k = 0; k < P::NACC; ++k) pp[k] = v[k];
           pp[P::NACC] = __int_as_float(cg);
+          if (P::WRITES) pp[P::NACC + 1] = __int_as_float(wl ? (wtot > a.fl_K ? -1 : wtot) : -1);
         }
       } else if (vi && sub == 0) {
         P::finalize(a, pi, v);
@@ -1495,6 +1606,7 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
   a.dt_shift = c->dt_shift.as<float4>();
   a.n_count = c->n_count.as<int>();
   a.n_sbase = c->n_sbase.as<long long>();
+  a.n_child0 = c->n_child0.as<int>();
   a.n_hmax = c->n_hmax.as<float>();
   a.b_hmax = c->b_hmax.as<float>();
   a.n_lo = c->n_lo.as<float4>();
@@ -1543,8 +1655,14 @@ int run_sweep(sph_ctx* c, int phase, int only_active, int counting, cudaStream_t
         SPH_TRY(dbuf_ensure(c->fl_blk, sizeof(int) * (size_t)c->nblock));
         SPH_TRY(dbuf_ensure(c->fl_over, 64));
         SPH_CUDA(cudaMemsetAsync(c->fl_blk.p, 0, sizeof(int) * (size_t)c->nblock, s));
-        SPH_CUDA(cudaMemsetAsync(c->fl_over.p, 0, sizeof(int), s));
+        SPH_CUDA(cudaMemsetAsync(c->fl_over.p, 0, 2 * sizeof(int), s));
         c->fl_K = c->prm.pair_list_cap;
+        a.sl_list = nullptr;
+        if (c->part_cols > 0) {  // lists of the slices of blocks cut into work units
+          const size_t cols = (size_t)((c->part_cols + 31) / 32) * 32;
+          SPH_TRY(dbuf_ensure(c->sl_list, sizeof(unsigned) * cols * c->prm.pair_list_cap));
+          a.sl_list = c->sl_list.as<unsigned>();
+        }
         a.fl_list = c->fl_list.as<unsigned>();
         a.fl_cnt = c->fl_cnt.as<int>();
         a.fl_flag = c->fl_flag.as<int>();

@@ -223,6 +223,8 @@ class SPH:
         d["sweep_units"] = list(st.sweep_units)
         d["sweep_candidates"] = list(st.sweep_candidates)
         d["sweep_gathered"] = list(st.sweep_gathered)
+        d["pairs_unlisted"] = st.pairs_unlisted
+        d["pairs_unlisted_cut"] = st.pairs_unlisted_cut
         d["newton_active"] = list(st.newton_active)
         return d
 
