@@ -76,23 +76,27 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
-def profiled_traffic(phase_name):
-    """DRAM bytes per launch of a sweep phase from the committed ncu summary,
-    or None when the sweep kernel source changed since that capture."""
+def profiled_traffic(phase_name, units_per_launch):
+    """DRAM bytes per launch of a sweep phase: the bytes per accepted unit
+    from the committed ncu summary of a smaller case of the same field law
+    (dram__bytes_read.sum + dram__bytes_write.sum over all the phase's
+    launches of one step, divided by the units those launches accepted),
+    times this run's units per launch; None when the sweep kernel source
+    changed since that capture."""
     import hashlib
     import re
     src = os.path.join(ROOT, "paper_1404_2303_gb300", "csrc", "sweep.cu")
-    summ = os.path.join(ROOT, "profiles", "sweep_kernels_multires128.md")
+    summ = os.path.join(ROOT, "profiles", "traffic_sweeps_lognormal128.md")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         text = open(summ).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256: ([0-9a-f]{64})", text)
-    t = re.search(r"traffic_bytes_per_launch\[" + re.escape(phase_name) + r"\]: ([0-9.eE+]+)", text)
+    t = re.search(r"traffic_bytes_per_unit\[" + re.escape(phase_name) + r"\]: ([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != sha:
         return None
-    return float(t.group(1))
+    return float(t.group(1)) * units_per_launch
 
 
 def peaks():
@@ -591,7 +595,7 @@ def main():
         achieved = k["units_per_launch"] * INSTR[dom] / (k["ms_per_launch"] / 1e3)
         roof = {"kernel": PHASE_KERNELS[dom], "bound": "alu", "achieved": achieved / 1e12,
                 "peak": peak_alu / 1e12, "unit": "T FP32-instr/s",
-                "frac": achieved / peak_alu, "traffic": profiled_traffic(dname),
+                "frac": achieved / peak_alu, "traffic": profiled_traffic(dname, k["units_per_launch"]),
                 "peak_source": f"{sms} SMs (device attribute) x {LANES} FP32 lanes x "
                                f"{sm_max:.0f} MHz (sm_max_mhz of {pk_kind} peaks)",
                 "instr_per_unit": INSTR[dom]}

@@ -1067,51 +1067,74 @@ __global__ void __launch_bounds__(256, P::MINB) k_sweep(SweepArgs a) {
         const int excl = incl - jn;
         const int total = __shfl_sync(FULL, incl, 31);
         if (COUNT && a.units) ngath += total;
-        for (int f0 = 0; f0 < total; f0 += 32) {
-          const int f = f0 + lane;
-          int k = 0;
+        // UNR entries per lane per step, their chains of dependent loads
+        // (index, then position) in flight together; the force-like phases,
+        // at their register limit, take one
+        constexpr int UNR = P::USES_HJ ? 1 : 2;
+        for (int f0 = 0; f0 < total; f0 += 32 * UNR) {
+          int jx[UNR];
+          float4 pv[UNR];
+          bool tk[UNR];
+          float shx[UNR], shy[UNR], shz[UNR], ck2[UNR];
 #pragma unroll
-          for (int step = 16; step > 0; step >>= 1) {
-            int v = __shfl_sync(FULL, excl, k + step);
-            if (v <= f) k += step;
-          }
-          const long long jbk = __shfl_sync(FULL, jb, k);
-          const int jsk = __shfl_sync(FULL, js, k);
-          const int exk = __shfl_sync(FULL, excl, k);
-          const float sx = __shfl_sync(FULL, sh.x, k), sy = __shfl_sync(FULL, sh.y, k),
-                      sz = __shfl_sync(FULL, sh.z, k);
-          const float Ck2 = __shfl_sync(FULL, C2, k);
-          bool take = false;
-          int jidx = 0;
-          float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (f < total) {
-            jidx = a.s_idx[jbk + jsk + (f - exk)];
-            const float4 q = a.pos4[jidx];
-            pj = make_float4(__fadd_rn(q.x, sx), __fadd_rn(q.y, sy), __fadd_rn(q.z, sz), q.w);
-            const float dx = fmaxf(fmaxf(bx0 - pj.x, pj.x - bx1), 0.f);
-            const float dy = fmaxf(fmaxf(by0 - pj.y, pj.y - by1), 0.f);
-            const float dz = fmaxf(fmaxf(bz0 - pj.z, pj.z - bz1), 0.f);
-            float lim2 = Ck2;
-            if (P::USES_HJ) {
-              // r < max(h_i, h_j): a j reaches the chunk only through its own h
-              const float cj = fmaxf(hmx, a.h[jidx]) + a.delta;
-              lim2 = cj * cj;
+          for (int u = 0; u < UNR; ++u) {
+            const int f = f0 + 32 * u + lane;
+            int k = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+              int v = __shfl_sync(FULL, excl, k + step);
+              if (v <= f) k += step;
             }
-            take = a.naive || fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= lim2;
+            const long long jbk = __shfl_sync(FULL, jb, k);
+            const int jsk = __shfl_sync(FULL, js, k);
+            const int exk = __shfl_sync(FULL, excl, k);
+            shx[u] = __shfl_sync(FULL, sh.x, k);
+            shy[u] = __shfl_sync(FULL, sh.y, k);
+            shz[u] = __shfl_sync(FULL, sh.z, k);
+            ck2[u] = __shfl_sync(FULL, C2, k);
+            jx[u] = f < total ? a.s_idx[jbk + jsk + (f - exk)] : -1;
           }
-          const unsigned mt = __ballot_sync(FULL, take);
-          const int nt = __popc(mt);
-          if (staged + nt > cap) {
-            compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot, a.fl_K,
-                                         sub, G);
-            if (COUNT && vi && sub < staged) ncand += (staged - sub + G - 1) / G;
-            fold<P>(acc, cmp, part, a.kahan);
-            staged = 0;
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            tk[u] = false;
+            pv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (jx[u] >= 0) {
+              const float4 q = a.pos4[jx[u]];
+              pv[u] = make_float4(__fadd_rn(q.x, shx[u]), __fadd_rn(q.y, shy[u]),
+                                  __fadd_rn(q.z, shz[u]), q.w);
+            }
           }
-          if (take)
-            P::stage(a, jidx, P::WRITES ? make_tag(jidx, sx, sy, sz) : 0u, pj, buf,
-                     staged + __popc(mt & lt), cap);
-          staged += nt;
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            if (jx[u] >= 0) {
+              const float4 pj = pv[u];
+              const float dx = fmaxf(fmaxf(bx0 - pj.x, pj.x - bx1), 0.f);
+              const float dy = fmaxf(fmaxf(by0 - pj.y, pj.y - by1), 0.f);
+              const float dz = fmaxf(fmaxf(bz0 - pj.z, pj.z - bz1), 0.f);
+              float lim2 = ck2[u];
+              if (P::USES_HJ) {
+                const float cj = fmaxf(hmx, a.h[jx[u]]) + a.delta;
+                lim2 = cj * cj;
+              }
+              tk[u] = a.naive || fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= lim2;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            const unsigned mt = __ballot_sync(FULL, tk[u]);
+            const int nt = __popc(mt);
+            if (staged + nt > cap) {
+              compute_pass<P, COUNT, LIST>(I, vi, buf, lst, staged, cap, part, cnt, wl, wtot,
+                                           a.fl_K, sub, G);
+              if (COUNT && vi && sub < staged) ncand += (staged - sub + G - 1) / G;
+              fold<P>(acc, cmp, part, a.kahan);
+              staged = 0;
+            }
+            if (tk[u])
+              P::stage(a, jx[u], P::WRITES ? make_tag(jx[u], shx[u], shy[u], shz[u]) : 0u, pv[u],
+                       buf, staged + __popc(mt & lt), cap);
+            staged += nt;
+          }
         }
       };
       // fraction of a target box (shifted) inside the chunk's box grown by C
