@@ -127,6 +127,12 @@ __device__ double hermite_root(double p0, double m0, double p1, double m1) {
   return (b - a) < 1e-6 ? 0.5 * (a + b) : -1.0;
 }
 
+// |ln(a / b)| for the step-size bookkeeping, in FP32 (the bracket ends and
+// h are FP32 values held in FP64; FP64 transcendentals are slow here)
+__device__ __forceinline__ float log_ratio(double a, double b) {
+  return fabsf(log1pf((float)(a - b) / (float)b));
+}
+
 __global__ void k_hsolve_update(long long n, HSolve S) {
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= n) return;
@@ -204,26 +210,32 @@ __global__ void k_hsolve_update(long long n, HSolve S) {
       // cubic Hermite interpolation of g over [ln L, ln H]: accurate to the
       // fourth order in the bracket width, so its root is taken even when it
       // lies far from the current end (no step-length test)
-      const double w = log(H / L);
+      // (increments relative to L kept exact: the bracket can be a few
+      // FP32 ulps wide)
+      const float x = (float)((H - L) / L);
+      const double w = (double)log1pf(x);
       const double t = hermite_root((double)gb.x, (double)gb.y * w, (double)gb.z, (double)gb.w * w);
       if (t > 0.0 && t < 1.0) {
-        const double q = L * exp(t * w);
+        const double q = L + L * (double)expm1f((float)(t * w));
         if (q > L && q < H) hn = q;
       }
     }
-    if (hn > 0) {
-      step = (float)fabs(log(hn / hd));
-    } else {
-      hn = L > 0 ? sqrt(L * H) : 0.5 * (L + H);  // bisection (geometric once L > 0)
-      step = (float)fabs(log(hn / hd));
+    if (!(hn > 0)) {  // bisection (geometric once L > 0)
+      if (L > 0) {
+        const float x = (float)((H - L) / L);
+        hn = L + L * (double)(x / (sqrtf(1.f + x) + 1.f));
+      } else {
+        hn = 0.5 * (L + H);
+      }
     }
+    step = log_ratio(hn, hd);
   } else {
     // no upper end yet: Newton upwards, doubling when it has no slope, capped
     // at the cell limit (evaluated there once before declaring the limit)
     hn = slope > 1e-3f ? hd * (double)__expf(-dx) : 2.0 * hd;
     if (!(hn > L)) hn = 2.0 * hd;
     hn = fmin(hn, hl);
-    step = (float)fabs(log(hn / hd));
+    step = log_ratio(hn, hd);
   }
   S.lo[s] = L;
   S.hi[s] = H;
