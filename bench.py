@@ -381,18 +381,43 @@ def small_parity(dev, n=4096, seed=29):
     return out
 
 
-def oracle_full_rate():
-    """The oracle on the whole 16^3 jittered lattice (all host cores): units
-    (directed density interactions + unordered force pairs) per second."""
-    from oracle import sph_oracle as O
+def _oracle_box(name):
     import synth.configs as C
-    d = C.uniform_lattice(16, seed=1)
+    if name == "lattice16":
+        return C.uniform_lattice(16, seed=1), "the whole 16^3 jittered lattice (4096 particles)"
+    return C.sinusoid(64, seed=4), "the whole 64^3 sinusoid box (262,144 particles)"
+
+
+def oracle_full_rate(name="lattice16"):
+    """The oracle on a whole box (its neighbour queries on all host cores):
+    units (directed density interactions + unordered force pairs) per
+    second, tree build included."""
+    from oracle import sph_oracle as O
+    d, what = _oracle_box(name)
     t0 = time.perf_counter()
     f = O.evaluate(d["x"], d["m"], d["u"], h_guess=d["h_guess"])
     dt = time.perf_counter() - t0
     units = float(f["count"].sum() + 0.5 * f["force_count"].sum())
-    return {"value": units / dt, "seconds": dt, "units": units,
-            "sample": "the whole 16^3 jittered lattice (4096 particles), tree build included"}
+    return {"value": units / dt, "seconds": dt, "units": units, "sample": what + ", tree build included"}
+
+
+def _one_core_rate(name, q):
+    os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    q.put(oracle_full_rate(name))
+
+
+def oracle_full_rate_one_core(name="lattice16"):
+    """The same on one host core: a spawned process pinned to one CPU (the
+    neighbour-query threads then share it)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    pr = ctx.Process(target=_one_core_rate, args=(name, q))
+    pr.start()
+    r = q.get(timeout=600)
+    pr.join()
+    r["cores"] = 1
+    return r
 
 
 def main():
@@ -407,6 +432,8 @@ def main():
     ap.add_argument("--others", default="multires128,batch64,sinusoid64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=64)
+    ap.add_argument("--oracle-c4", action="store_true",
+                    help="also time the oracle on the whole 64^3 sinusoid box, all cores and one")
     ap.add_argument("--kahan", type=int, default=1)
     ap.add_argument("--block-max", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
@@ -682,6 +709,10 @@ def main():
                              "included)"}
             try:
                 cpu["whole_small_box"] = oracle_full_rate()
+                cpu["whole_small_box_one_core"] = oracle_full_rate_one_core()
+                if args.oracle_c4:  # minutes of CPU time: on request only
+                    cpu["whole_sinusoid64"] = oracle_full_rate("sinusoid64")
+                    cpu["whole_sinusoid64_one_core"] = oracle_full_rate_one_core("sinusoid64")
             except Exception as e:  # noqa: BLE001
                 cpu["whole_small_box"] = {"failed": str(e)}
             # the oracle's values of that sample against this run's results

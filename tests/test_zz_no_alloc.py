@@ -9,12 +9,14 @@ here cannot hide another test; it also passes alone in a fresh process.
 Both calls of a pair must agree with the regular path within the density /
 smoothing-length tolerance of the parity tests (1e-5 relative): the second
 call checks that what the shared array keeps from the first call does not
-leak into the next result."""
+leak into the next result.  The first call is also held to the FP64 oracle
+(the definition both paths approximate) at the same tolerance."""
 import numpy as np
 import pytest
 import torch
 
 import synth.configs as C
+from oracle import sph_oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +47,8 @@ def test_noalloc_matches_regular_entry_point_twice(make):
     ref = s.density(m)
     h_ref = ref["h"].cpu().numpy().astype(np.float64)
     rho_ref = ref["rho"].cpu().numpy().astype(np.float64)
+    orc = O.evaluate(d["x"], d["m"], np.ones(len(d["m"])),
+                     h_guess=None if d["h_guess"] is None else d["h_guess"].astype(np.float64))
     for call in range(2):
         h, rho, iters = density_small_noalloc(pos, m, h_guess=hg)
         torch.cuda.synchronize()
@@ -53,6 +57,9 @@ def test_noalloc_matches_regular_entry_point_twice(make):
         assert iters >= 1
         assert np.max(np.abs(h - h_ref) / h_ref) <= TOL, call
         assert np.max(np.abs(rho - rho_ref) / rho_ref) <= TOL, call
+        if call == 0:
+            assert np.max(np.abs(h - orc["h"]) / orc["h"]) <= TOL
+            assert np.max(np.abs(rho - orc["rho"]) / orc["rho"]) <= TOL
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
