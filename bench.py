@@ -99,6 +99,22 @@ def profiled_traffic(phase_name, units_per_launch):
     return float(t.group(1)) * units_per_launch
 
 
+def build_rate(st, n, pk, pk_kind):
+    """One decomposition build against the HBM copy bandwidth: algorithmic
+    bytes n (24 + 12 + 8) (positions in, keys, FP32 relative positions and
+    permutation out) + 2 x 13 x 8 n (the 13 sorted lists of (key, index)
+    written and read once) over the mean build time of the profiled pass
+    (stages timed with a stream synchronisation at each boundary)."""
+    builds = max(1, int(st.get("builds", 0)))
+    ms = sum(st["build_ms"]) / builds
+    alg = float(n) * (24 + 12 + 8) + 2.0 * 13 * 8 * float(n)
+    gbs = alg / (ms / 1e3) / 1e9 if ms > 0 else None
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    return {"ms_per_build": ms, "builds_in_profiled_pass": builds, "algorithmic_bytes": alg,
+            "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak if gbs else None,
+            "peak_source": f"hbm_gbs of {pk_kind} peaks"}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -771,6 +787,7 @@ def main():
             "h_iteration_active": [x for x in prod["stats"]["newton_active"] if x],
             "sampled_parity": parity,
             "build_stages_ms": {BUILD_STAGES[k]: st["build_ms"][k] / prof["steps"] for k in range(8)},
+            "build": build_rate(st, n, pk, pk_kind),
             "cpu_baseline": cpu,
         }
         line.update(extras)
