@@ -411,10 +411,15 @@ def oracle_full_rate(name="lattice16"):
     from oracle import sph_oracle as O
     d, what = _oracle_box(name)
     t0 = time.perf_counter()
+    O.Neighbours(d["x"], 1.0)  # the neighbour tree alone, timed apart
+    t_tree = time.perf_counter() - t0
+    t0 = time.perf_counter()
     f = O.evaluate(d["x"], d["m"], d["u"], h_guess=d["h_guess"])
     dt = time.perf_counter() - t0
     units = float(f["count"].sum() + 0.5 * f["force_count"].sum())
-    return {"value": units / dt, "seconds": dt, "units": units, "sample": what + ", tree build included"}
+    return {"value": units / dt, "seconds": dt, "units": units, "sample": what + ", tree build included",
+            "tree_build_seconds": t_tree,
+            "value_without_tree_build": units / max(dt - t_tree, 1e-9)}
 
 
 def _one_core_rate(name, q):
