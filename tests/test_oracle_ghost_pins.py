@@ -3,8 +3,8 @@ and of the magnitude of its force and heating (Eq. (dvdt), (dudt)) against
 facts fixed by thermodynamics and calculus rather than by re-typing the
 formulas:
 
-* d rho/dh equals the central finite difference of rho(h) at fixed
-  positions (Eq. (rho) evaluated at h(1 +- e));
+* d rho/dh and dN/dh equal the central finite differences of rho(h) and
+  N(h) at fixed positions (Eq. (rho), (nneigh) evaluated at h(1 +- e));
 * for equal masses the h of Eq. (nneigh) keeps rho h^3 fixed, so
   Omega = 1 + h/(3 rho) d rho/dh must equal h N'(h) / (3 N), with N'(h)
   from finite differences of a brute-force neighbour sum;
@@ -79,6 +79,18 @@ def test_drho_dh_is_the_derivative_of_rho():
     rm = O.density_at(f["nb"], m, h * (1 - e))["rho"]
     fd = (rp - rm) / (2 * e * h)
     assert np.allclose(f["drho_dh"], fd, rtol=1e-7, atol=1e-7 * np.abs(fd).max())
+
+
+def test_dn_dh_is_the_derivative_of_the_neighbour_number():
+    # the slope the h iteration steps with (Eq. (nneigh) differentiated in h)
+    d = C.random_box(500, 19, "clumped")
+    m = d["m"].astype(np.float64)
+    f = O.evaluate(d["x"], m, d["u"], h_guess=0.2)
+    h, e = f["h"], 1e-6
+    npl = O.density_at(f["nb"], m, h * (1 + e))["nngb"]
+    nmi = O.density_at(f["nb"], m, h * (1 - e))["nngb"]
+    fd = (npl - nmi) / (2 * e * h)
+    assert np.allclose(f["dnngb_dh"], fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
 
 
 def test_omega_equals_log_derivative_of_the_neighbour_number():
